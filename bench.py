@@ -1,0 +1,355 @@
+"""Benchmark: exact Smith-Waterman/Gotoh protein database search on GB300.
+
+Workload (default): 20 queries of 144-5478 residues (log-spaced) against a
+synthetic database of 570,000 subjects with lognormal lengths (mean 360,
+~205 M residues), BLOSUM62, gap open 10 / extend 2 -- the shape of the
+paper's search (Section IV-A), synthetic because Env-NR is not available.
+
+One step = one exact search of all queries against the whole database
+through a plan (persistent packed 16-bit kernel + int32 long-subject and
+recompute work, replayed from a CUDA graph).  Printed: one JSON line with
+GCUPS (cells = sum of query lengths x sum of subject lengths), per-step
+latency p50/p99, the plain int32 one-query-per-launch baseline, the integer
+roofline of the search kernel against the intpeak microbenchmark, the end-to-
+end rate through the C ABI with host buffers, and the CPU oracle timed on a
+bounded sample on the host cores.
+
+``--impl reference`` times the CPU oracle instead (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GCUPS on 1 GB300 (batched packed vs plain int32), bit-exact scores; p50/p99 latency"
+WORKLOADS = ("paper-search", "plain-small", "batched-uneven", "long")
+
+# algorithmic integer lane-operations per cell of the packed recurrence:
+# per 32-bit word (2 cells) vmax(E,F), viaddmax_relu (H), vsub (H-Go),
+# viaddmax (E'), viaddmax (F'), half a vimax3 (S), one prmt (profile pair)
+PACKED_OPS_PER_CELL = 6.5 / 2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="paper-search", choices=WORKLOADS)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--rows", type=int, default=None, help="packed rows per thread (16/32)")
+    ap.add_argument("--cutoff", type=int, default=None, help="inter/intra length cutoff")
+    ap.add_argument("--warps", type=int, default=None)
+    ap.add_argument("--cpu-sample", type=float, default=0.01,
+                    help="fraction of subjects the CPU oracle baseline searches")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload(name, seed):
+    from paper_2309_09609_gb300 import synth
+    return {"paper-search": synth.paper_search, "plain-small": synth.plain_small,
+            "batched-uneven": synth.batched_uneven, "long": synth.long_sequences}[name](seed)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device=0):
+        self.device = device
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc or not self.file:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(power) if power else None}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("SWGB_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend)
+        return rank, world, local, dist
+    return rank, world, local, None
+
+
+def max_over_ranks(x, dist, device):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64,
+                     device=device if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample(w, frac, seed=0):
+    """All queries vs the first `frac` of subjects (by caller index)."""
+    n = max(1, int(round(frac * len(w.db))))
+    sub = w.db.subset(np.arange(n))
+    return sub
+
+
+def time_oracle(w, sub, nthreads):
+    import oracle
+    nq, nd = len(w.queries), len(sub)
+    pq = np.repeat(np.arange(nq, dtype=np.int32), nd)
+    pd = np.tile(np.arange(nd, dtype=np.int64), nq)
+    t0 = time.perf_counter()
+    s = oracle.pairs_packed(w.queries.res, w.queries.offs, w.queries.lens, sub.res, sub.offs,
+                            sub.lens, pq, pd, w.gap_open, w.gap_extend, None, nthreads)
+    dt = time.perf_counter() - t0
+    cells = w.queries.total * sub.total
+    return s.reshape(nq, nd), cells, dt
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle, as it stands, on the host cores."""
+    rank, world, local, dist = dist_setup(args)
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    w = make_workload(args.workload, args.seed)
+    frac = min(args.cpu_sample, 0.002) if args.workload == "paper-search" else args.cpu_sample
+    sub = oracle_sample(w, frac)
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        time_oracle(w, sub, cores)
+    times = []
+    for _ in range(args.steps):
+        _, cells, dt = time_oracle(w, sub, cores)
+        times.append(dt)
+    ms = 1e3 * statistics.mean(times)
+    g = cells / (ms / 1e3) / 1e9
+    out = {"impl": "reference", "metric": METRIC, "value": round(g, 4), "unit": "GCUPS",
+           "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
+           "data": "synthetic",
+           "config": {"workload": w.name, "sample": f"all {len(w.queries)} queries x first "
+                      f"{len(sub)} subjects ({cells:.3e} cells per step)"},
+           "cpu_baseline": {"value": round(g, 4), "unit": "GCUPS", "cores": cores,
+                            "kind": "oracle", "sample": f"{len(sub)} subjects x all queries"},
+           "e2e": {"value": round(g, 4), "unit": "GCUPS", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_native(args):
+    import torch
+    rank, world, local, dist = dist_setup(args)
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2309_09609_gb300 import swgb
+
+    w = make_workload(args.workload, args.seed)
+    q, db = w.queries, w.db
+    nq, N = len(q), len(db)
+    cells = w.cells
+    t0 = time.perf_counter()
+    d = swgb.Database.from_seqset(db, device=local)
+    db_create_s = time.perf_counter() - t0
+    opts = {}
+    if args.rows:
+        opts["rows_per_thread"] = args.rows
+    if args.cutoff is not None:
+        opts["long_cutoff"] = args.cutoff
+    if args.warps:
+        opts["warps_per_block"] = args.warps
+    plan = d.plan(nq, q.total, **opts)
+    stream = torch.cuda.Stream(device=device)
+    q_dev = torch.from_numpy(q.res).to(device)
+    l_dev = torch.from_numpy(q.lens).to(device)
+    out = torch.empty((nq, N), dtype=torch.int32, device=device)
+
+    def step():
+        plan.search(q_dev, l_dev, w.gap_open, w.gap_extend, None, out=out, stream=stream)
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+
+    # timed region: device-resident inputs (the DB layouts, ~2 x residues bytes,
+    # exceed the 129 MB L2, so no flush is needed between steps)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    kernel_ms, recompute_ms = [], []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        evs[0].record(stream)
+        for i in range(args.steps):
+            step()
+            evs[i + 1].record(stream)
+            st = plan.stats()
+            kernel_ms.append(st["search_ms"])
+            recompute_ms.append(st["recompute_ms"])
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    total_ms = max_over_ranks(total_ms, dist, device)
+    ms = total_ms / args.steps
+    gcups = world * cells / (ms / 1e3) / 1e9
+    stats = plan.stats()
+    clocks = clk.summary()
+
+    result = {"metric": METRIC, "value": round(gcups, 2), "unit": "GCUPS", "n_gpus": world,
+              "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+              "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+              "dtype": "i16x2+i32", "data": "synthetic",
+              "config": {"workload": w.name, "queries": nq, "subjects": N,
+                         "query_residues": q.total, "db_residues": db.total, "cells": cells,
+                         "gaps": [w.gap_open, w.gap_extend], "matrix": "BLOSUM62",
+                         "planted_homologs": int(w.planted.size),
+                         "l2": "no flush: device-resident DB layouts (~2x DB residues bytes) > 129 MB L2",
+                         "parallelism": f"replicas{world}" if world > 1 else "1 GPU",
+                         "plan": {k: getattr(swgb.options(**opts), k) for k, _ in swgb.Options._fields_}},
+              "latency_ms": {"p50": round(float(np.percentile(step_ms, 50)), 3),
+                             "p99": round(float(np.percentile(step_ms, 99)), 3)},
+              "recomputed_pairs": stats["recomputed_pairs"],
+              "db_create_s": round(db_create_s, 3),
+              "gpu_launches": stats["kernels_launched"] * args.steps,
+              "clocks": clocks}
+
+    # roofline of the dominant kernel: integer lane-ops vs the intpeak microbenchmark
+    kms = statistics.mean(kernel_ms) if kernel_ms else float("nan")
+    inter_cells = cells  # every cell is issued by the packed recurrence except long subjects
+    achieved = PACKED_OPS_PER_CELL * inter_cells / (kms / 1e3) / 1e12
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    mix, mix_mhz, _ = swgb.intpeak("cell_s16x2_prmt", 8, 256, 20000)
+    max_mhz = clocks.get("sm_max_mhz") or 2070.0
+    peak = mix * sms * max_mhz * 1e6 / 1e12
+    result["roofline"] = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
+                          "unit": "Tops/s", "frac": round(achieved / peak, 4), "traffic": None,
+                          "kernel": "search_kernel (mode 0)", "kernel_ms": round(kms, 3),
+                          "ops_per_cell": PACKED_OPS_PER_CELL,
+                          "peak_source": f"intpeak cell_s16x2_prmt {mix:.1f} lane-ops/clk/SM x "
+                                         f"{sms} SMs x {max_mhz:.0f} MHz (max SM clock)",
+                          "intpeak_clock_mhz": round(mix_mhz, 1),
+                          "recompute_ms": round(statistics.mean(recompute_ms), 3)}
+
+    # plain int32 one-query-per-launch baseline on the same workload
+    if not args.no_plain:
+        outp = torch.empty_like(out)
+        d.search_plain(q_dev, l_dev, w.gap_open, w.gap_extend, out=outp, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d.search_plain(q_dev, l_dev, w.gap_open, w.gap_extend, out=outp, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1)
+        pg = cells / (pms / 1e3) / 1e9
+        result["plain_int32"] = {"value": round(pg, 2), "unit": "GCUPS", "ms": round(pms, 3),
+                                 "launches": nq}
+        result["speedup_vs_plain"] = round(gcups / world / pg, 3)
+        result["plain_equals_packed"] = bool(torch.equal(outp, out))
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    q_host = torch.from_numpy(q.res).pin_memory()
+    l_host = torch.from_numpy(q.lens).pin_memory()
+    out_host = torch.empty((nq, N), dtype=torch.int32).pin_memory()
+    plan.search(q_host, l_host, w.gap_open, w.gap_extend, None, out=out_host)
+    e2e = []
+    for _ in range(max(1, min(args.steps, 3))):
+        t0 = time.perf_counter()
+        plan.search(q_host, l_host, w.gap_open, w.gap_extend, None, out=out_host)
+        e2e.append(time.perf_counter() - t0)
+    e2e_s = max_over_ranks(statistics.mean(e2e), dist, device)
+    result["e2e"] = {"value": round(world * cells / e2e_s / 1e9, 2), "unit": "GCUPS",
+                     "h2d_bytes_per_step": int(q.total + 4 * nq),
+                     "d2h_bytes_per_step": int(4 * nq * N), "ms_per_step": round(1e3 * e2e_s, 3)}
+
+    # CPU oracle on a bounded sample (rank 0, N = 1): baseline and parity check
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        sub = oracle_sample(w, args.cpu_sample)
+        cores = os.cpu_count() or 1
+        ref, ocells, odt = time_oracle(w, sub, cores)
+        got = out_host.numpy()[:, :len(sub)]
+        result["cpu_baseline"] = {"value": round(ocells / odt / 1e9, 4), "unit": "GCUPS",
+                                  "cores": cores, "kind": "oracle",
+                                  "sample": f"all {nq} queries x first {len(sub)} subjects "
+                                            f"({ocells:.3e} cells, {odt:.1f} s)"}
+        result["parity_on_cpu_sample"] = bool((got == ref).all())
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

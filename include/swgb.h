@@ -1,0 +1,186 @@
+/*
+ * swgb.h -- C ABI of libswgb: exact Smith-Waterman/Gotoh protein database
+ * search on one NVIDIA GB300 (sm_103a).
+ *
+ * The library computes, for every (query, subject) pair, the optimal local
+ * alignment score of arxiv 2309.09609, Section II-B, Eq. 1-3:
+ *
+ *   H(i,j) = max(0, H(i-1,j-1) + SM(Q[i], D[j]), E(i,j), F(i,j))
+ *   E(i,j) = max(H(i,j-1) - Go, E(i,j-1) - Ge)
+ *   F(i,j) = max(H(i-1,j) - Go, F(i-1,j) - Ge)
+ *   score  = max over all cells of H  (H is 0 on row and column 0)
+ *
+ * in integer arithmetic, exactly (bit for bit) -- the database search of
+ * Section III-A with BLOSUM62 and integer scores (Section IV-A).
+ *
+ * Conventions shared by every call:
+ *   - Residues are codes 0..23 in the BLOSUM62 order
+ *     A R N D C Q E G H I L K M F P S T W Y V B Z X *  (sw_encode maps text).
+ *   - Gaps: (gap_open, gap_extend) with a gap of k residues costing
+ *     gap_open + k * gap_extend, i.e. Go = gap_open + gap_extend and
+ *     Ge = gap_extend in Eq. 2-3.  Both must be >= 0.  The paper's "10/2"
+ *     (Section IV-A) is gap_open = 10, gap_extend = 2 here.
+ *   - matrix: 24 x 24 int8, row-major, matrix[a * 24 + b] = SM(a, b) with a the
+ *     query residue and b the subject residue; NULL selects BLOSUM62.
+ *   - scores: int32, n_queries x n_subjects, row-major, subjects in the order
+ *     given to sw_db_create.  Zero-length sequences score 0.
+ *   - Pointers may be host or device memory unless stated; the library
+ *     detects which.  Inputs are borrowed for the duration of the call only.
+ *   - Every call returns a status; on failure sw_last_error() describes it.
+ *     No call aborts the process, traps on the device or waits unboundedly.
+ */
+#ifndef SWGB_H
+#define SWGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SW_OK = 0,
+  SW_EINVAL = 1,     /* bad argument: residue code >= 24, negative length, NULL ... */
+  SW_ENOMEM = 2,     /* device or host allocation failed */
+  SW_ECUDA = 3,      /* a CUDA runtime call failed */
+  SW_ETIMEDOUT = 4,  /* a bounded device-side wait gave up */
+  SW_EBUSY = 5       /* the plan's capacity is exceeded or it is in use */
+} sw_status;
+
+/* Opaque handle: a protein database resident in device memory. */
+typedef struct sw_db sw_db;
+
+/* Opaque handle: a reusable search context (device buffers + CUDA graph). */
+typedef struct sw_plan sw_plan;
+
+/* Thread-local text of the last error on this thread ("" if none). */
+const char* sw_last_error(void);
+
+/* Maps n ASCII letters to residue codes (Section IV-A scores with BLOSUM62,
+ * whose 24 symbols define the alphabet).  Lower case is folded; U, O, J and
+ * any other byte map to X (code 22).  text and out are host memory. */
+sw_status sw_encode(const char* text, int64_t n, uint8_t* out);
+
+/* Copies the library's built-in BLOSUM62 (24 x 24 int8, row-major) to out
+ * (host memory, 576 bytes). */
+void sw_default_matrix(int8_t* out);
+
+/* Builds the device database (Section III-A: the database is split by
+ * length into an inter-task part of short subjects and an intra-task part of
+ * long ones).
+ *   residues: concatenated codes of all subjects, sum(lengths) bytes, host.
+ *   lengths:  n_subjects int32 lengths (>= 0), host.
+ *   device:   CUDA device ordinal.
+ * The subjects are sorted by length and laid out twice on the device: in
+ * groups of 64 subjects interleaved 8 residues at a time (inter-task kernel)
+ * and contiguously (intra-task and recompute kernels).  Inputs are copied;
+ * the handle owns all device memory until sw_db_destroy.
+ * Errors: SW_EINVAL for a code >= 24, a negative length or n_subjects < 0;
+ * SW_ENOMEM; SW_ECUDA. */
+sw_status sw_db_create(const uint8_t* residues, const int32_t* lengths, int64_t n_subjects,
+                       int device, sw_db** out);
+
+/* Frees the database.  NULL-safe.  No plan of this database may be used after. */
+void sw_db_destroy(sw_db* db);
+
+/* Number of subjects / residues / the longest subject length. */
+int64_t sw_db_subjects(const sw_db* db);
+int64_t sw_db_residues(const sw_db* db);
+int32_t sw_db_max_length(const sw_db* db);
+
+/* Tuning of the exact search; every field has a safe default (zero-init and
+ * call sw_options_default).  None of them changes a score. */
+typedef struct {
+  int32_t rows_per_thread;   /* query rows per thread in the packed inter-task kernel: 16 or 32 */
+  int32_t warps_per_block;   /* 4 or 8 */
+  int32_t long_cutoff;       /* subjects longer than this use the intra-task kernel */
+  int32_t intra_rows;        /* query rows per lane in the intra-task kernel: 8 or 16 */
+  int32_t use_graph;         /* 1: capture the launch sequence in a CUDA graph */
+  int32_t force_int32;       /* 1: all subjects through the int32 intra-task kernel */
+} sw_options;
+
+void sw_options_default(sw_options* opt);
+
+/* Statistics of the last search run through a plan. */
+typedef struct {
+  int64_t cells;             /* sum(query lengths) * sum(subject lengths) */
+  int64_t inter_items;       /* (query, group of 64 subjects) work items */
+  int64_t intra_items;       /* (query, long subject) work items */
+  int64_t recomputed_pairs;  /* pairs whose 16-bit score saturated, redone in int32 */
+  int32_t timed_out;         /* 1 if a bounded device wait gave up */
+  int32_t kernels_launched;  /* kernels of this library launched by the search */
+  float search_ms;           /* device time of the persistent search kernel (CUDA events) */
+  float recompute_ms;        /* device time of the int32 recompute kernel (CUDA events) */
+} sw_stats;
+
+/* Creates a search context for up to max_queries queries holding up to
+ * max_query_residues residues in total, on the database's device.  All
+ * device memory the search needs (query buffer, border scratch, saturation
+ * list, work counters) is allocated here, once.  opt may be NULL.
+ * Errors: SW_EINVAL, SW_ENOMEM, SW_ECUDA. */
+sw_status sw_plan_create(sw_db* db, int32_t max_queries, int64_t max_query_residues,
+                         const sw_options* opt, sw_plan** out);
+
+void sw_plan_destroy(sw_plan* plan);
+
+/* Exact scores of every query against every subject (Eq. 1-3), the batched
+ * path: one persistent launch over all (query, subject-group) work items,
+ * longest first, scored as packed 16-bit pairs (two subjects per 32-bit
+ * word) with every pair whose 16-bit score may have saturated recomputed in
+ * int32, plus long subjects in the int32 intra-task kernel; the launch
+ * sequence is replayed from a CUDA graph when opt.use_graph is set.
+ *   queries:   concatenated query codes (sum(q_lengths) bytes), host or device.
+ *   q_lengths: n_queries int32, host or device.
+ *   scores:    n_queries x n_subjects int32, host or device, written in full.
+ *   stream:    cudaStream_t to run on (NULL: the legacy default stream).
+ * The call returns after the scores are in `scores` (it synchronises the
+ * stream).  One plan serves one call at a time (SW_EBUSY otherwise).
+ * Errors: SW_EINVAL (bad code, length, gap or size), SW_EBUSY (capacity),
+ * SW_ECUDA, SW_ETIMEDOUT. */
+sw_status sw_plan_search(sw_plan* plan, const uint8_t* queries, const int32_t* q_lengths,
+                         int32_t n_queries, int32_t gap_open, int32_t gap_extend,
+                         const int8_t* matrix, int32_t* scores, void* stream);
+
+/* Like sw_plan_search but returns as soon as the work is queued on the
+ * stream; queries/q_lengths must be host memory (copied before return) and
+ * scores device memory; completion is observed with sw_plan_wait or any CUDA
+ * stream/event query.  Used by the serving loop to overlap requests. */
+sw_status sw_plan_search_async(sw_plan* plan, const uint8_t* queries, const int32_t* q_lengths,
+                               int32_t n_queries, int32_t gap_open, int32_t gap_extend,
+                               const int8_t* matrix, int32_t* scores, void* stream);
+
+/* Waits for the plan's last asynchronous search, at most timeout_ms
+ * milliseconds (0: only poll; negative: no bound); SW_ETIMEDOUT if it is
+ * still running when the time is up. */
+sw_status sw_plan_wait(sw_plan* plan, int32_t timeout_ms);
+
+/* Statistics of the plan's last completed search. */
+sw_status sw_plan_stats(const sw_plan* plan, sw_stats* out);
+
+/* One-shot exact search: creates a plan sized for this call, runs
+ * sw_plan_search and frees it.  Same arguments and errors as sw_plan_search. */
+sw_status sw_search(sw_db* db, const uint8_t* queries, const int32_t* q_lengths,
+                    int32_t n_queries, int32_t gap_open, int32_t gap_extend,
+                    const int8_t* matrix, int32_t* scores, void* stream);
+
+/* The plain baseline of Algorithm 1: int32 cells, one thread per subject,
+ * one kernel launch per query, no packing, no long-subject kernel.  Same
+ * arguments, result and errors as sw_search. */
+sw_status sw_search_plain(sw_db* db, const uint8_t* queries, const int32_t* q_lengths,
+                          int32_t n_queries, int32_t gap_open, int32_t gap_extend,
+                          const int8_t* matrix, int32_t* scores, void* stream);
+
+/* Integer-pipe microbenchmark (Section III-B, Eq. 4: the throughput term,
+ * measured instead of looked up).  op selects an instruction kind (0 iadd,
+ * 1 imax, 2 viaddmax_s32, 3 viaddmax_s16x2, 4 viaddmax_s16x2_relu,
+ * 5 vimax3_s16x2, 6 vmaxs2, 7 vsub2, 8 vaddss2, 9 prmt, 10 packed cell pair,
+ * 11 packed cell pair + prmt, 12 int32 cell); results (host memory):
+ * out[0] lane-operations per SM clock, out[1] SM clock in MHz, out[2] seconds. */
+sw_status sw_intpeak(int32_t op, int32_t blocks_per_sm, int32_t threads, int32_t iters,
+                     double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWGB_H */

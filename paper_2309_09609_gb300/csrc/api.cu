@@ -1,0 +1,801 @@
+// api.cu -- host side of libswgb: the C ABI of include/swgb.h.
+//
+//   * sw_db_create: sorts subjects by length and builds the two device
+//     layouts (interleaved groups of 64 for the inter-task kernel, contiguous
+//     for the intra-task kernel); the split of the database by length into a
+//     short (inter-task) and long (intra-task) part follows Section III-A.
+//   * sw_plan_*: a reusable search context.  All device memory is allocated
+//     once; per search only the query block and a parameter block are copied,
+//     and the kernel sequence (reset counters, persistent search, int32
+//     recompute of saturated pairs) is replayed from one CUDA graph.
+//   * sw_search_plain: the int32 baseline, one kernel launch per query.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <thread>
+#include <vector>
+
+#include "swgb_internal.h"
+
+using namespace swgb;
+
+// ---- errors ---------------------------------------------------------------------
+namespace swgb {
+static thread_local char g_err[512] = "";
+
+sw_status sw_set_error(sw_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+sw_status sw_set_cuda_error(cudaError_t err, const char* where) {
+  cudaGetLastError();  // clear a sticky launch error so the context stays usable
+  return sw_set_error(err == cudaErrorMemoryAllocation ? SW_ENOMEM : SW_ECUDA, "%s: %s", where,
+                      cudaGetErrorString(err));
+}
+
+void sw_clear_error() { g_err[0] = 0; }
+}  // namespace swgb
+
+extern "C" const char* sw_last_error(void) { return g_err; }
+
+// ---- alphabet and BLOSUM62 ------------------------------------------------------
+static const char kAlphabet[] = "ARNDCQEGHILKMFPSTWYVBZX*";
+static constexpr int kCodeX = 22;
+
+extern "C" sw_status sw_encode(const char* text, int64_t n, uint8_t* out) {
+  if (n < 0 || (n > 0 && (!text || !out))) return sw_set_error(SW_EINVAL, "sw_encode: bad arguments");
+  int8_t table[256];
+  for (int i = 0; i < 256; i++) table[i] = kCodeX;
+  for (int c = 0; c < ALPHA; c++) {
+    const unsigned char u = (unsigned char)kAlphabet[c];
+    table[u] = (int8_t)c;
+    if (u >= 'A' && u <= 'Z') table[u - 'A' + 'a'] = (int8_t)c;
+  }
+  for (int64_t i = 0; i < n; i++) out[i] = (uint8_t)table[(unsigned char)text[i]];
+  return SW_OK;
+}
+
+// BLOSUM62 (Henikoff & Henikoff 1992), NCBI table in the order of kAlphabet.
+// The paper searches with BLOSUM62 (Section IV-A) without printing it.
+static const int8_t kBlosum62[ALPHA * ALPHA] = {
+    4,  -1, -2, -2, 0,  -1, -1, 0,  -2, -1, -1, -1, -1, -2, -1, 1,  0,  -3, -2, 0,  -2, -1, 0,  -4,
+    -1, 5,  0,  -2, -3, 1,  0,  -2, 0,  -3, -2, 2,  -1, -3, -2, -1, -1, -3, -2, -3, -1, 0,  -1, -4,
+    -2, 0,  6,  1,  -3, 0,  0,  0,  1,  -3, -3, 0,  -2, -3, -2, 1,  0,  -4, -2, -3, 3,  0,  -1, -4,
+    -2, -2, 1,  6,  -3, 0,  2,  -1, -1, -3, -4, -1, -3, -3, -1, 0,  -1, -4, -3, -3, 4,  1,  -1, -4,
+    0,  -3, -3, -3, 9,  -3, -4, -3, -3, -1, -1, -3, -1, -2, -3, -1, -1, -2, -2, -1, -3, -3, -2, -4,
+    -1, 1,  0,  0,  -3, 5,  2,  -2, 0,  -3, -2, 1,  0,  -3, -1, 0,  -1, -2, -1, -2, 0,  3,  -1, -4,
+    -1, 0,  0,  2,  -4, 2,  5,  -2, 0,  -3, -3, 1,  -2, -3, -1, 0,  -1, -3, -2, -2, 1,  4,  -1, -4,
+    0,  -2, 0,  -1, -3, -2, -2, 6,  -2, -4, -4, -2, -3, -3, -2, 0,  -2, -2, -3, -3, -1, -2, -1, -4,
+    -2, 0,  1,  -1, -3, 0,  0,  -2, 8,  -3, -3, -1, -2, -1, -2, -1, -2, -2, 2,  -3, 0,  0,  -1, -4,
+    -1, -3, -3, -3, -1, -3, -3, -4, -3, 4,  2,  -3, 1,  0,  -3, -2, -1, -3, -1, 3,  -3, -3, -1, -4,
+    -1, -2, -3, -4, -1, -2, -3, -4, -3, 2,  4,  -2, 2,  0,  -3, -2, -1, -2, -1, 1,  -4, -3, -1, -4,
+    -1, 2,  0,  -1, -3, 1,  1,  -2, -1, -3, -2, 5,  -1, -3, -1, 0,  -1, -3, -2, -2, 0,  1,  -1, -4,
+    -1, -1, -2, -3, -1, 0,  -2, -3, -2, 1,  2,  -1, 5,  0,  -2, -1, -1, -1, -1, 1,  -3, -1, -1, -4,
+    -2, -3, -3, -3, -2, -3, -3, -3, -1, 0,  0,  -3, 0,  6,  -4, -2, -2, 1,  3,  -1, -3, -3, -1, -4,
+    -1, -2, -2, -1, -3, -1, -1, -2, -2, -3, -3, -1, -2, -4, 7,  -1, -1, -4, -3, -2, -2, -1, -2, -4,
+    1,  -1, 1,  0,  -1, 0,  0,  0,  -1, -2, -2, 0,  -1, -2, -1, 4,  1,  -3, -2, -2, 0,  0,  0,  -4,
+    0,  -1, 0,  -1, -1, -1, -1, -2, -2, -1, -1, -1, -1, -2, -1, 1,  5,  -2, -2, 0,  -1, -1, 0,  -4,
+    -3, -3, -4, -4, -2, -2, -3, -2, -2, -3, -2, -3, -1, 1,  -4, -3, -2, 11, 2,  -3, -4, -3, -2, -4,
+    -2, -2, -2, -3, -2, -1, -2, -3, 2,  -1, -1, -2, -1, 3,  -3, -2, -2, 2,  7,  -1, -3, -2, -1, -4,
+    0,  -3, -3, -3, -1, -2, -2, -3, -3, 3,  1,  -2, 1,  -1, -2, -2, 0,  -3, -1, 4,  -3, -2, -1, -4,
+    -2, -1, 3,  4,  -3, 0,  1,  -1, 0,  -3, -4, 0,  -3, -3, -2, 0,  -1, -4, -3, -3, 4,  1,  -1, -4,
+    -1, 0,  0,  1,  -3, 3,  4,  -2, 0,  -3, -3, 1,  -1, -3, -1, 0,  -1, -3, -2, -2, 1,  4,  -1, -4,
+    0,  -1, -1, -1, -2, -1, -1, -1, -1, -1, -1, -1, -1, -1, -2, 0,  0,  -2, -1, -1, -1, -1, -1, -4,
+    -4, -4, -4, -4, -4, -4, -4, -4, -4, -4, -4, -4, -4, -4, -4, -4, -4, -4, -4, -4, -4, -4, -4, 1,
+};
+
+extern "C" void sw_default_matrix(int8_t* out) {
+  if (out) memcpy(out, kBlosum62, sizeof kBlosum62);
+}
+
+extern "C" void sw_options_default(sw_options* opt) {
+  if (!opt) return;
+  opt->rows_per_thread = 32;
+  opt->warps_per_block = 8;
+  opt->long_cutoff = 3000;
+  opt->intra_rows = 8;
+  opt->use_graph = 1;
+  opt->force_int32 = 0;
+}
+
+// ---- small helpers ----------------------------------------------------------------
+static bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+static cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+static int parallel_threads() {
+  unsigned h = std::thread::hardware_concurrency();
+  return (int)std::max(1u, std::min(h, 32u));
+}
+
+template <typename F>
+static void parallel_for(int64_t n, F f) {
+  const int nt = (int)std::min<int64_t>(parallel_threads(), std::max<int64_t>(n, 1));
+  if (nt <= 1) {
+    for (int64_t i = 0; i < n; i++) f(i);
+    return;
+  }
+  std::atomic<int64_t> next(0);
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; t++)
+    th.emplace_back([&]() {
+      for (;;) {
+        const int64_t lo = next.fetch_add(64);
+        if (lo >= n) break;
+        const int64_t hi = std::min(n, lo + 64);
+        for (int64_t i = lo; i < hi; i++) f(i);
+      }
+    });
+  for (auto& x : th) x.join();
+}
+
+// ---- database -----------------------------------------------------------------------
+struct sw_db {
+  int device = 0;
+  DbView view{};
+  std::vector<int32_t> glen_h;   // padded group lengths (host copy)
+  std::vector<int32_t> clen_h;   // sorted lengths (host copy)
+  int64_t residues = 0;
+  // owned device buffers
+  uint8_t* inter = nullptr;
+  int64_t* goff = nullptr;
+  int32_t* glen = nullptr;
+  uint8_t* cont = nullptr;
+  int64_t* coff = nullptr;
+  int32_t* clen = nullptr;
+  int32_t* perm = nullptr;
+};
+
+static void db_free(sw_db* db) {
+  if (!db) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(db->device);
+  cudaFree(db->inter);
+  cudaFree(db->goff);
+  cudaFree(db->glen);
+  cudaFree(db->cont);
+  cudaFree(db->coff);
+  cudaFree(db->clen);
+  cudaFree(db->perm);
+  cudaSetDevice(cur);
+  delete db;
+}
+
+extern "C" sw_status sw_db_create(const uint8_t* residues, const int32_t* lengths,
+                                  int64_t n_subjects, int device, sw_db** out) {
+  sw_clear_error();
+  if (!out) return sw_set_error(SW_EINVAL, "sw_db_create: out is NULL");
+  *out = nullptr;
+  if (n_subjects < 0 || n_subjects > (int64_t)INT32_MAX - GROUP)
+    return sw_set_error(SW_EINVAL, "sw_db_create: n_subjects %lld out of range", (long long)n_subjects);
+  if (n_subjects > 0 && !lengths) return sw_set_error(SW_EINVAL, "sw_db_create: lengths is NULL");
+  const int64_t N = n_subjects;
+  std::vector<int64_t> off(N);
+  int64_t total = 0;
+  int32_t max_len = 0;
+  for (int64_t i = 0; i < N; i++) {
+    if (lengths[i] < 0) return sw_set_error(SW_EINVAL, "sw_db_create: length[%lld] < 0", (long long)i);
+    off[i] = total;
+    total += lengths[i];
+    max_len = std::max(max_len, lengths[i]);
+  }
+  if (total > 0 && !residues) return sw_set_error(SW_EINVAL, "sw_db_create: residues is NULL");
+  for (int64_t i = 0; i < total; i++)
+    if (residues[i] >= ALPHA)
+      return sw_set_error(SW_EINVAL, "sw_db_create: residue code %d at %lld (codes are 0..23)",
+                          (int)residues[i], (long long)i);
+  CUDA_TRY(cudaSetDevice(device));
+
+  // sort by length, longest first (stable: ties keep caller order)
+  std::vector<int32_t> order(N);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int32_t a, int32_t b) { return lengths[a] > lengths[b]; });
+  const int32_t G = (int32_t)((N + GROUP - 1) / GROUP);
+  std::vector<int32_t> glen(G), clen(N), perm((size_t)G * GROUP, -1);
+  std::vector<int64_t> goff(G), coff(N);
+  int64_t inter_bytes = 0, c = 0;
+  for (int32_t g = 0; g < G; g++) {
+    const int32_t L = lengths[order[(size_t)g * GROUP]];  // the group's longest
+    glen[g] = (L + CHUNK - 1) / CHUNK * CHUNK;
+    goff[g] = inter_bytes;
+    inter_bytes += (int64_t)glen[g] * GROUP;
+  }
+  for (int64_t s = 0; s < N; s++) {
+    perm[s] = order[s];
+    clen[s] = lengths[order[s]];
+    coff[s] = c;
+    c += clen[s];
+  }
+  std::vector<uint8_t> inter((size_t)std::max<int64_t>(inter_bytes, 1)), cont((size_t)std::max<int64_t>(total, 1));
+  parallel_for(G, [&](int64_t g) {
+    uint8_t* base = inter.data() + goff[g];
+    const int32_t L = glen[g];
+    for (int k = 0; k < GROUP; k++) {
+      const int64_t s = g * GROUP + k;
+      const uint8_t* src = s < N ? residues + off[order[s]] : nullptr;
+      const int32_t len = s < N ? lengths[order[s]] : 0;
+      uint8_t* dst = base + (k >> 1) * 16 + (k & 1) * 8;
+      for (int32_t j = 0; j < L; j++)
+        dst[(int64_t)(j / CHUNK) * CHUNK_BYTES + (j % CHUNK)] = j < len ? src[j] : (uint8_t)PAD_CODE;
+    }
+  });
+  parallel_for(N, [&](int64_t s) {
+    if (clen[s]) memcpy(cont.data() + coff[s], residues + off[order[s]], (size_t)clen[s]);
+  });
+
+  sw_db* db = new sw_db();
+  db->device = device;
+  db->residues = total;
+  cudaError_t e = cudaSuccess;
+#define DB_ALLOC_COPY(dst, src, count)                                                     \
+  if (e == cudaSuccess) e = dalloc(&db->dst, (count));                                     \
+  if (e == cudaSuccess && (count) > 0)                                                     \
+    e = cudaMemcpy(db->dst, (src), sizeof(*db->dst) * (size_t)(count), cudaMemcpyHostToDevice);
+  DB_ALLOC_COPY(inter, inter.data(), inter_bytes);
+  DB_ALLOC_COPY(goff, goff.data(), G);
+  DB_ALLOC_COPY(glen, glen.data(), G);
+  DB_ALLOC_COPY(cont, cont.data(), total);
+  DB_ALLOC_COPY(coff, coff.data(), N);
+  DB_ALLOC_COPY(clen, clen.data(), N);
+  DB_ALLOC_COPY(perm, perm.data(), (int64_t)G * GROUP);
+#undef DB_ALLOC_COPY
+  if (e != cudaSuccess) {
+    sw_status st = sw_set_cuda_error(e, "sw_db_create: device upload");
+    db_free(db);
+    return st;
+  }
+  db->view.inter = db->inter;
+  db->view.goff = db->goff;
+  db->view.glen = db->glen;
+  db->view.cont = db->cont;
+  db->view.coff = db->coff;
+  db->view.clen = db->clen;
+  db->view.perm = db->perm;
+  db->view.n = N;
+  db->view.groups = G;
+  db->view.max_len = max_len;
+  db->glen_h = std::move(glen);
+  db->clen_h = std::move(clen);
+  *out = db;
+  return SW_OK;
+}
+
+extern "C" void sw_db_destroy(sw_db* db) { db_free(db); }
+extern "C" int64_t sw_db_subjects(const sw_db* db) { return db ? db->view.n : 0; }
+extern "C" int64_t sw_db_residues(const sw_db* db) { return db ? db->residues : 0; }
+extern "C" int32_t sw_db_max_length(const sw_db* db) { return db ? db->view.max_len : 0; }
+
+// ---- query batch validation and parameter block ------------------------------------
+struct HostBatch {
+  std::vector<uint8_t> res_copy;  // only when the caller's queries live on the device
+  std::vector<int32_t> len;
+  std::vector<int64_t> off;
+  std::vector<int32_t> order;
+  const uint8_t* res = nullptr;   // host view of the residues
+  int64_t total = 0;
+  bool res_on_device = false;
+};
+
+static sw_status read_batch(const uint8_t* queries, const int32_t* q_lengths, int32_t nq,
+                            HostBatch& hb) {
+  if (nq < 0) return sw_set_error(SW_EINVAL, "n_queries < 0");
+  if (nq > 0 && !q_lengths) return sw_set_error(SW_EINVAL, "q_lengths is NULL");
+  hb.len.resize(nq);
+  if (nq > 0) {
+    if (is_device_ptr(q_lengths)) {
+      CUDA_TRY(cudaMemcpy(hb.len.data(), q_lengths, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost));
+    } else {
+      memcpy(hb.len.data(), q_lengths, sizeof(int32_t) * nq);
+    }
+  }
+  hb.off.resize(nq);
+  hb.total = 0;
+  for (int32_t i = 0; i < nq; i++) {
+    if (hb.len[i] < 0) return sw_set_error(SW_EINVAL, "q_lengths[%d] < 0", i);
+    hb.off[i] = hb.total;
+    hb.total += hb.len[i];
+  }
+  if (hb.total > 0 && !queries) return sw_set_error(SW_EINVAL, "queries is NULL");
+  hb.res_on_device = hb.total > 0 && is_device_ptr(queries);
+  if (hb.res_on_device) {
+    hb.res_copy.resize(hb.total);
+    CUDA_TRY(cudaMemcpy(hb.res_copy.data(), queries, hb.total, cudaMemcpyDeviceToHost));
+    hb.res = hb.res_copy.data();
+  } else {
+    hb.res = queries;
+  }
+  for (int64_t i = 0; i < hb.total; i++)
+    if (hb.res[i] >= ALPHA)
+      return sw_set_error(SW_EINVAL, "query residue code %d at %lld (codes are 0..23)",
+                          (int)hb.res[i], (long long)i);
+  hb.order.resize(nq);
+  std::iota(hb.order.begin(), hb.order.end(), 0);
+  std::stable_sort(hb.order.begin(), hb.order.end(),
+                   [&](int32_t a, int32_t b) { return hb.len[a] > hb.len[b]; });
+  return SW_OK;
+}
+
+// Largest gap penalty sum kept on the packed 16-bit path: E and F stay
+// >= -(Go + Ge) >= -32768 there.
+static constexpr int kPackedMaxGap = 16384;
+static constexpr int kMaxGap = 100000000;
+
+static sw_status fill_scoring(SearchParams& P, int32_t gap_open, int32_t gap_extend,
+                              const int8_t* matrix, bool* packed_ok) {
+  if (gap_open < 0 || gap_extend < 0 || gap_open > kMaxGap || gap_extend > kMaxGap)
+    return sw_set_error(SW_EINVAL, "gap penalties must be in [0, %d]", kMaxGap);
+  int8_t m[ALPHA * ALPHA];
+  if (matrix) {
+    if (is_device_ptr(matrix)) {
+      CUDA_TRY(cudaMemcpy(m, matrix, sizeof m, cudaMemcpyDeviceToHost));
+    } else {
+      memcpy(m, matrix, sizeof m);
+    }
+  } else {
+    memcpy(m, kBlosum62, sizeof m);
+  }
+  int maxsm = 0;
+  for (int a = 0; a < NCODES; a++)
+    for (int b = 0; b < NCODES; b++)
+      P.sm[a * NCODES + b] = (a < ALPHA && b < ALPHA) ? m[a * ALPHA + b] : (int8_t)PAD_SCORE;
+  for (int i = 0; i < ALPHA * ALPHA; i++) maxsm = std::max(maxsm, (int)m[i]);
+  P.go = gap_open + gap_extend;
+  P.ge = gap_extend;
+  P.sat_threshold = S16_LIMIT - maxsm;
+  *packed_ok = (P.go + P.ge) <= kPackedMaxGap;
+  return SW_OK;
+}
+
+// ---- plan ---------------------------------------------------------------------------------
+struct sw_plan {
+  sw_db* db = nullptr;
+  sw_options opt{};
+  KernelConfig kc{};
+  int32_t max_queries = 0;
+  int64_t max_residues = 0;
+  int32_t g_first = 0;      // first inter-task group under the cutoff
+  // device buffers
+  uint8_t* qres = nullptr;
+  int64_t* qoff = nullptr;
+  int32_t* qlen = nullptr;
+  int32_t* qorder = nullptr;
+  int32_t* scores_dev = nullptr;  // used when the caller's scores live on the host
+  SearchParams* params = nullptr;
+  SearchState* state = nullptr;
+  Scratch scr{};
+  // pinned host staging
+  SearchParams* params_h = nullptr;
+  SearchState* state_h = nullptr;
+  uint8_t* qres_h = nullptr;
+  int64_t* qoff_h = nullptr;
+  int32_t* qlen_h = nullptr;
+  int32_t* qorder_h = nullptr;
+  // graph
+  cudaGraphExec_t graph = nullptr;
+  cudaEvent_t done = nullptr;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // before search, after search, after recompute
+  bool in_flight = false;
+  sw_stats stats{};
+  sw_stats pending{};
+};
+
+static void plan_free(sw_plan* p) {
+  if (!p) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (p->db) cudaSetDevice(p->db->device);
+  if (p->graph) cudaGraphExecDestroy(p->graph);
+  if (p->done) cudaEventDestroy(p->done);
+  for (auto& e : p->ev)
+    if (e) cudaEventDestroy(e);
+  cudaFree(p->qres);
+  cudaFree(p->qoff);
+  cudaFree(p->qlen);
+  cudaFree(p->qorder);
+  cudaFree(p->scores_dev);
+  cudaFree(p->params);
+  cudaFree(p->state);
+  cudaFree(p->scr.inter_border);
+  cudaFree(p->scr.intra_border);
+  cudaFree(p->scr.flags);
+  cudaFreeHost(p->params_h);
+  cudaFreeHost(p->state_h);
+  cudaFreeHost(p->qres_h);
+  cudaFreeHost(p->qoff_h);
+  cudaFreeHost(p->qlen_h);
+  cudaFreeHost(p->qorder_h);
+  cudaSetDevice(cur);
+  delete p;
+}
+
+extern "C" sw_status sw_plan_create(sw_db* db, int32_t max_queries, int64_t max_query_residues,
+                                    const sw_options* opt, sw_plan** out) {
+  sw_clear_error();
+  if (!out) return sw_set_error(SW_EINVAL, "sw_plan_create: out is NULL");
+  *out = nullptr;
+  if (!db) return sw_set_error(SW_EINVAL, "sw_plan_create: db is NULL");
+  if (max_queries < 1 || max_query_residues < 0)
+    return sw_set_error(SW_EINVAL, "sw_plan_create: bad capacity");
+  sw_options o;
+  sw_options_default(&o);
+  if (opt) o = *opt;
+  if (o.rows_per_thread != 16 && o.rows_per_thread != 32)
+    return sw_set_error(SW_EINVAL, "rows_per_thread must be 16 or 32");
+  if (o.intra_rows != 8 && o.intra_rows != 16)
+    return sw_set_error(SW_EINVAL, "intra_rows must be 8 or 16");
+  if (o.warps_per_block < 1 || o.warps_per_block > 8)
+    return sw_set_error(SW_EINVAL, "warps_per_block must be 1..8");
+  if (o.long_cutoff < 0) return sw_set_error(SW_EINVAL, "long_cutoff < 0");
+  CUDA_TRY(cudaSetDevice(db->device));
+
+  sw_plan* p = new sw_plan();
+  p->db = db;
+  p->opt = o;
+  p->max_queries = max_queries;
+  p->max_residues = max_query_residues;
+  const DbView& v = db->view;
+  // groups whose longest subject exceeds the cutoff go to the intra-task kernel
+  int32_t gf = 0;
+  if (o.force_int32) {
+    gf = v.groups;
+  } else {
+    while (gf < v.groups && db->glen_h[gf] > o.long_cutoff) gf++;
+  }
+  p->g_first = gf;
+  const int32_t L_inter = gf < v.groups ? db->glen_h[gf] : 0;
+
+  int dev_sms = 0;
+  cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, db->device);
+  const int bps = search_blocks_per_sm(o.rows_per_thread, o.intra_rows, o.warps_per_block);
+  if (bps < 1) {
+    plan_free(p);
+    return sw_set_error(SW_ECUDA, "search kernel cannot launch with %d warps (rows %d/%d)",
+                        o.warps_per_block, o.rows_per_thread, o.intra_rows);
+  }
+  p->kc.rows = o.rows_per_thread;
+  p->kc.intra_rows = o.intra_rows;
+  p->kc.warps = o.warps_per_block;
+  p->kc.blocks = dev_sms * bps;
+  p->kc.smem = search_smem_bytes(o.rows_per_thread, o.intra_rows, o.warps_per_block);
+  const int64_t W = (int64_t)p->kc.blocks * p->kc.warps;
+
+  cudaError_t e = cudaSuccess;
+  const int64_t nres = std::max<int64_t>(max_query_residues, 1);
+  p->scr.inter_stride_vec = (int64_t)(L_inter / CHUNK) * 4 * 32;
+  p->scr.intra_stride = std::max(v.max_len, 1);
+  p->scr.flag_capacity = (int64_t)max_queries * std::max<int64_t>(v.n, 1);
+  if (e == cudaSuccess) e = dalloc(&p->qres, nres);
+  if (e == cudaSuccess) e = dalloc(&p->qoff, max_queries);
+  if (e == cudaSuccess) e = dalloc(&p->qlen, max_queries);
+  if (e == cudaSuccess) e = dalloc(&p->qorder, max_queries);
+  if (e == cudaSuccess) e = dalloc(&p->scores_dev, (size_t)max_queries * std::max<int64_t>(v.n, 1));
+  if (e == cudaSuccess) e = dalloc(&p->params, 1);
+  if (e == cudaSuccess) e = dalloc(&p->state, 1);
+  if (e == cudaSuccess) e = dalloc(&p->scr.inter_border, (size_t)(W * std::max<int64_t>(p->scr.inter_stride_vec, 1)));
+  if (e == cudaSuccess) e = dalloc(&p->scr.intra_border, (size_t)(W * p->scr.intra_stride));
+  if (e == cudaSuccess) e = dalloc(&p->scr.flags, (size_t)p->scr.flag_capacity);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&p->params_h, sizeof(SearchParams));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&p->state_h, sizeof(SearchState));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&p->qres_h, nres);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&p->qoff_h, sizeof(int64_t) * max_queries);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&p->qlen_h, sizeof(int32_t) * max_queries);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&p->qorder_h, sizeof(int32_t) * max_queries);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming);
+  for (auto& ev : p->ev)
+    if (e == cudaSuccess) e = cudaEventCreate(&ev);
+  if (e != cudaSuccess) {
+    sw_status st = sw_set_cuda_error(e, "sw_plan_create: allocation");
+    plan_free(p);
+    return st;
+  }
+  memset(p->params_h, 0, sizeof(SearchParams));
+  *out = p;
+  return SW_OK;
+}
+
+extern "C" void sw_plan_destroy(sw_plan* plan) {
+  if (plan && plan->in_flight) cudaEventSynchronize(plan->done);
+  plan_free(plan);
+}
+
+// The device work of one search: reset counters, persistent search, recompute.
+// Events around the two kernels give their device time on the launching
+// stream (inside a captured graph they become event-record nodes).
+// (cudaEventRecordExternal makes them real event-record nodes under capture).
+static cudaError_t enqueue_kernels(sw_plan* p, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(p->state, 0, sizeof(SearchState), s);
+  if (e == cudaSuccess) e = cudaEventRecordWithFlags(p->ev[0], s, cudaEventRecordExternal);
+  if (e == cudaSuccess) e = launch_search(p->kc, 0, p->db->view, p->params, p->state, p->scr, s);
+  if (e == cudaSuccess) e = cudaEventRecordWithFlags(p->ev[1], s, cudaEventRecordExternal);
+  if (e == cudaSuccess) e = launch_search(p->kc, 1, p->db->view, p->params, p->state, p->scr, s);
+  if (e == cudaSuccess) e = cudaEventRecordWithFlags(p->ev[2], s, cudaEventRecordExternal);
+  return e;
+}
+
+static cudaError_t run_kernels(sw_plan* p, cudaStream_t s) {
+  if (!p->opt.use_graph) return enqueue_kernels(p, s);
+  if (!p->graph) {
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e2 = enqueue_kernels(p, cs);
+      e = cudaStreamEndCapture(cs, &g);
+      if (e2 != cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&p->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+      p->graph = nullptr;
+      return e;
+    }
+  }
+  return cudaGraphLaunch(p->graph, s);
+}
+
+// Stages a batch into the plan and enqueues everything up to (not including)
+// the copy of the scores to a host buffer.
+static sw_status plan_enqueue(sw_plan* p, const HostBatch& hb, int32_t nq, int32_t gap_open,
+                              int32_t gap_extend, const int8_t* matrix, int32_t* scores_dev,
+                              cudaStream_t s) {
+  if (nq > p->max_queries || hb.total > p->max_residues)
+    return sw_set_error(SW_EBUSY, "batch (%d queries, %lld residues) exceeds the plan (%d, %lld)",
+                        nq, (long long)hb.total, p->max_queries, (long long)p->max_residues);
+  SearchParams& P = *p->params_h;
+  bool packed_ok = true;
+  sw_status st = fill_scoring(P, gap_open, gap_extend, matrix, &packed_ok);
+  if (st != SW_OK) return st;
+  const DbView& v = p->db->view;
+  const int32_t gf = packed_ok ? p->g_first : v.groups;
+  const int64_t n_long = std::min<int64_t>(v.n, (int64_t)gf * GROUP);
+  P.qres = p->qres;
+  P.qoff = p->qoff;
+  P.qlen = p->qlen;
+  P.qorder = p->qorder;
+  P.scores = scores_dev;
+  P.nq = nq;
+  P.n_long = (int32_t)n_long;
+  P.g_first = gf;
+  P.n_intra_items = n_long * nq;
+  P.n_inter_items = (int64_t)(v.groups - gf) * nq;
+  memcpy(p->qoff_h, hb.off.data(), sizeof(int64_t) * nq);
+  memcpy(p->qlen_h, hb.len.data(), sizeof(int32_t) * nq);
+  memcpy(p->qorder_h, hb.order.data(), sizeof(int32_t) * nq);
+  if (hb.total > 0) memcpy(p->qres_h, hb.res, (size_t)hb.total);
+  CUDA_TRY(cudaMemcpyAsync(p->qres, p->qres_h, (size_t)std::max<int64_t>(hb.total, 1), cudaMemcpyHostToDevice, s));
+  if (nq > 0) {
+    CUDA_TRY(cudaMemcpyAsync(p->qoff, p->qoff_h, sizeof(int64_t) * nq, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(p->qlen, p->qlen_h, sizeof(int32_t) * nq, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(p->qorder, p->qorder_h, sizeof(int32_t) * nq, cudaMemcpyHostToDevice, s));
+  }
+  CUDA_TRY(cudaMemcpyAsync(p->params, p->params_h, sizeof(SearchParams), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(run_kernels(p, s));
+  CUDA_TRY(cudaMemcpyAsync(p->state_h, p->state, sizeof(SearchState), cudaMemcpyDeviceToHost, s));
+  p->pending = sw_stats{};
+  int64_t qsum = hb.total;
+  p->pending.cells = qsum * p->db->residues;
+  p->pending.inter_items = P.n_inter_items;
+  p->pending.intra_items = P.n_intra_items;
+  p->pending.kernels_launched = 2;
+  return SW_OK;
+}
+
+static void finish_stats(sw_plan* p) {
+  p->stats = p->pending;
+  if (cudaEventElapsedTime(&p->stats.search_ms, p->ev[0], p->ev[1]) != cudaSuccess ||
+      cudaEventElapsedTime(&p->stats.recompute_ms, p->ev[1], p->ev[2]) != cudaSuccess) {
+    cudaGetLastError();
+    p->stats.search_ms = p->stats.recompute_ms = -1.f;
+  }
+  p->stats.recomputed_pairs = (int64_t)std::min<unsigned long long>(
+      p->state_h->n_flags, (unsigned long long)p->scr.flag_capacity);
+  p->in_flight = false;
+}
+
+extern "C" sw_status sw_plan_search(sw_plan* plan, const uint8_t* queries, const int32_t* q_lengths,
+                                    int32_t n_queries, int32_t gap_open, int32_t gap_extend,
+                                    const int8_t* matrix, int32_t* scores, void* stream) {
+  sw_clear_error();
+  if (!plan) return sw_set_error(SW_EINVAL, "plan is NULL");
+  if (plan->in_flight) return sw_set_error(SW_EBUSY, "plan has a search in flight");
+  CUDA_TRY(cudaSetDevice(plan->db->device));
+  HostBatch hb;
+  sw_status st = read_batch(queries, q_lengths, n_queries, hb);
+  if (st != SW_OK) return st;
+  const int64_t N = plan->db->view.n;
+  if (n_queries > 0 && N > 0 && !scores) return sw_set_error(SW_EINVAL, "scores is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool dev_out = is_device_ptr(scores);
+  int32_t* target = dev_out ? scores : plan->scores_dev;
+  st = plan_enqueue(plan, hb, n_queries, gap_open, gap_extend, matrix, target, s);
+  if (st != SW_OK) return st;
+  plan->in_flight = true;
+  if (!dev_out && n_queries > 0 && N > 0)
+    CUDA_TRY(cudaMemcpyAsync(scores, plan->scores_dev, sizeof(int32_t) * (size_t)n_queries * N,
+                             cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaEventRecord(plan->done, s));
+  cudaError_t e = cudaEventSynchronize(plan->done);
+  finish_stats(plan);
+  if (e != cudaSuccess) return sw_set_cuda_error(e, "sw_plan_search");
+  CUDA_TRY(cudaGetLastError());
+  return SW_OK;
+}
+
+extern "C" sw_status sw_plan_search_async(sw_plan* plan, const uint8_t* queries,
+                                          const int32_t* q_lengths, int32_t n_queries,
+                                          int32_t gap_open, int32_t gap_extend,
+                                          const int8_t* matrix, int32_t* scores, void* stream) {
+  sw_clear_error();
+  if (!plan) return sw_set_error(SW_EINVAL, "plan is NULL");
+  if (plan->in_flight) return sw_set_error(SW_EBUSY, "plan has a search in flight");
+  CUDA_TRY(cudaSetDevice(plan->db->device));
+  HostBatch hb;
+  sw_status st = read_batch(queries, q_lengths, n_queries, hb);
+  if (st != SW_OK) return st;
+  if (n_queries > 0 && plan->db->view.n > 0 && !is_device_ptr(scores))
+    return sw_set_error(SW_EINVAL, "sw_plan_search_async needs device scores");
+  cudaStream_t s = (cudaStream_t)stream;
+  st = plan_enqueue(plan, hb, n_queries, gap_open, gap_extend, matrix, scores, s);
+  if (st != SW_OK) return st;
+  CUDA_TRY(cudaEventRecord(plan->done, s));
+  plan->in_flight = true;
+  return SW_OK;
+}
+
+extern "C" sw_status sw_plan_wait(sw_plan* plan, int32_t timeout_ms) {
+  if (!plan) return sw_set_error(SW_EINVAL, "plan is NULL");
+  if (!plan->in_flight) return SW_OK;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t e = cudaEventQuery(plan->done);
+    if (e == cudaSuccess) {
+      finish_stats(plan);
+      return SW_OK;
+    }
+    if (e != cudaErrorNotReady) {
+      plan->in_flight = false;
+      return sw_set_cuda_error(e, "sw_plan_wait");
+    }
+    if (timeout_ms >= 0) {
+      const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      if (ms >= timeout_ms) return sw_set_error(SW_ETIMEDOUT, "search still running after %d ms", timeout_ms);
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+extern "C" sw_status sw_plan_stats(const sw_plan* plan, sw_stats* out) {
+  if (!plan || !out) return sw_set_error(SW_EINVAL, "NULL argument");
+  *out = plan->stats;
+  return SW_OK;
+}
+
+extern "C" sw_status sw_search(sw_db* db, const uint8_t* queries, const int32_t* q_lengths,
+                               int32_t n_queries, int32_t gap_open, int32_t gap_extend,
+                               const int8_t* matrix, int32_t* scores, void* stream) {
+  sw_clear_error();
+  if (!db) return sw_set_error(SW_EINVAL, "db is NULL");
+  HostBatch hb;
+  sw_status st = read_batch(queries, q_lengths, n_queries, hb);
+  if (st != SW_OK) return st;
+  sw_plan* plan = nullptr;
+  sw_options o;
+  sw_options_default(&o);
+  o.use_graph = 0;
+  st = sw_plan_create(db, std::max(n_queries, 1), hb.total, &o, &plan);
+  if (st != SW_OK) return st;
+  st = sw_plan_search(plan, queries, q_lengths, n_queries, gap_open, gap_extend, matrix, scores,
+                      stream);
+  sw_plan_destroy(plan);
+  return st;
+}
+
+// ---- plain baseline ----------------------------------------------------------------------
+extern "C" sw_status sw_search_plain(sw_db* db, const uint8_t* queries, const int32_t* q_lengths,
+                                     int32_t n_queries, int32_t gap_open, int32_t gap_extend,
+                                     const int8_t* matrix, int32_t* scores, void* stream) {
+  sw_clear_error();
+  if (!db) return sw_set_error(SW_EINVAL, "db is NULL");
+  CUDA_TRY(cudaSetDevice(db->device));
+  HostBatch hb;
+  sw_status st = read_batch(queries, q_lengths, n_queries, hb);
+  if (st != SW_OK) return st;
+  const DbView& v = db->view;
+  const int64_t N = v.n;
+  if (n_queries > 0 && N > 0 && !scores) return sw_set_error(SW_EINVAL, "scores is NULL");
+  SearchParams P;
+  memset(&P, 0, sizeof P);
+  bool packed_ok;
+  st = fill_scoring(P, gap_open, gap_extend, matrix, &packed_ok);
+  if (st != SW_OK) return st;
+  if (n_queries == 0 || N == 0) return SW_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, db->device);
+  const int bps = std::max(1, std::min(plain_blocks_per_sm(), 8));
+  const int grid = (int)std::min<int64_t>((int64_t)sms * bps, v.groups);
+  std::vector<int64_t> boff(grid);
+  int64_t btotal = 0;
+  for (int b = 0; b < grid; b++) {
+    boff[b] = btotal;
+    btotal += (int64_t)db->glen_h[b] * GROUP;  // a block's first group is its longest
+  }
+  const bool dev_out = is_device_ptr(scores);
+  uint8_t* qres = nullptr;
+  int64_t *qoff = nullptr, *boff_d = nullptr;
+  int32_t *qlen = nullptr, *sc = nullptr;
+  int2* border = nullptr;
+  SearchParams* Pd = nullptr;
+  cudaError_t e = dalloc(&qres, hb.total);
+  if (e == cudaSuccess) e = dalloc(&qoff, n_queries);
+  if (e == cudaSuccess) e = dalloc(&qlen, n_queries);
+  if (e == cudaSuccess) e = dalloc(&boff_d, grid);
+  if (e == cudaSuccess) e = dalloc(&border, btotal);
+  if (e == cudaSuccess) e = dalloc(&Pd, 1);
+  if (e == cudaSuccess && !dev_out) e = dalloc(&sc, (size_t)n_queries * N);
+  if (e == cudaSuccess && hb.total > 0)
+    e = cudaMemcpyAsync(qres, hb.res, hb.total, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(qoff, hb.off.data(), sizeof(int64_t) * n_queries, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(qlen, hb.len.data(), sizeof(int32_t) * n_queries, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(boff_d, boff.data(), sizeof(int64_t) * grid, cudaMemcpyHostToDevice, s);
+  P.qres = qres;
+  P.qoff = qoff;
+  P.qlen = qlen;
+  P.scores = dev_out ? scores : sc;
+  P.nq = n_queries;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(Pd, &P, sizeof P, cudaMemcpyHostToDevice, s);
+  for (int32_t q = 0; q < n_queries && e == cudaSuccess; q++)
+    e = launch_plain(grid, v, Pd, q, border, boff_d, s);
+  if (e == cudaSuccess && !dev_out)
+    e = cudaMemcpyAsync(scores, sc, sizeof(int32_t) * (size_t)n_queries * N, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(qres);
+  cudaFree(qoff);
+  cudaFree(qlen);
+  cudaFree(boff_d);
+  cudaFree(border);
+  cudaFree(Pd);
+  cudaFree(sc);
+  if (e != cudaSuccess) return sw_set_cuda_error(e, "sw_search_plain");
+  return SW_OK;
+}
+
+// ---- microbenchmark ----------------------------------------------------------------------
+extern "C" sw_status sw_intpeak(int32_t op, int32_t blocks_per_sm, int32_t threads, int32_t iters,
+                                double* out) {
+  sw_clear_error();
+  if (!out) return sw_set_error(SW_EINVAL, "out is NULL");
+  int rc = intpeak_run(op, blocks_per_sm, threads, iters, &out[0], &out[1], &out[2]);
+  if (rc == SW_EINVAL) return sw_set_error(SW_EINVAL, "sw_intpeak: bad arguments");
+  return (sw_status)rc;
+}

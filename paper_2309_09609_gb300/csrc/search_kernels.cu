@@ -1,0 +1,508 @@
+// search_kernels.cu -- the alignment kernels of libswgb.
+//
+// All kernels compute Eq. 1-3 of arxiv 2309.09609 (Section II-B) in the
+// shared-gap form
+//
+//   h = max(hdiag + SM(q_i, d_j), E(i,j), F(i,j), 0)          (Eq. 1)
+//   t = h - Go
+//   E(i,j+1) = max(E(i,j) - Ge, t)                             (Eq. 2, next column)
+//   F(i+1,j) = max(F(i,j) - Ge, t)                             (Eq. 3, next row)
+//   S = max(S, h)
+//
+// which reorders Algorithm 1 so that H - Go is computed once per cell and E
+// and F are produced one step ahead (the paper's future work, Section VI,
+// names instruction reordering and narrower integers; this is both).
+//
+// Kernels:
+//   * search_kernel<T, TI>, mode 0 -- one persistent launch over work items
+//     taken longest-first from an atomic counter:
+//       - intra-task items (query, long subject): one warp per pair; lane k
+//         owns TI query rows of a 32*TI-row pass and sweeps the subject one
+//         step behind lane k-1, which hands it the (H, F) border of its last
+//         row through __shfl_up_sync (Section II-B: intra-task parallelism
+//         with neighbour border exchange).  int32 cells.
+//       - inter-task items (query, group of 64 short subjects): each lane owns
+//         two subjects, packed as the two 16-bit halves of every 32-bit word,
+//         and T query rows held in registers (Section II-B: inter-task
+//         parallelism, one matrix per processing element).  A pair whose
+//         16-bit score reaches 32767 - max(SM) is appended to a flag list.
+//   * search_kernel<T, TI>, mode 1 -- recomputes every flagged pair with the
+//     int32 intra-task code, so every score is exact.
+//   * plain_kernel -- the baseline: Algorithm 1 verbatim in int32, one thread
+//     per subject, one launch per query.
+//
+// No kernel waits on another thread, block or kernel: the only cross-warp
+// interaction is the atomic work counter, so nothing here can spin.
+#include <stdio.h>
+
+#include "swgb_internal.h"
+
+namespace swgb {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int MATRIX_SMEM = 640;  // 25 x 25 int8, rounded up to 16 bytes
+
+__device__ __forceinline__ uint32_t pack2(int v) {
+  return ((uint32_t)(uint16_t)(int16_t)v) * 0x00010001u;
+}
+
+// prmt with sign replication: result = (sext(a.byte k), sext(b.byte k)) as s16x2
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+  uint32_t r;
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(sel));
+  return r;
+}
+// selector for byte k: nibbles (low to high) k, 8|k, 4+k, 8|(4+k)
+__device__ __forceinline__ constexpr uint32_t sext_pair_sel(int k) {
+  return (uint32_t)(k | ((8 | k) << 4) | ((4 + k) << 8) | ((12 + k) << 12));
+}
+// int8 byte k of w, sign-extended to int32
+__device__ __forceinline__ int sext_byte(uint32_t w, int k) {
+  return (int)prmt(w, 0u, (uint32_t)(k | ((8 | k) << 4) | ((8 | k) << 8) | ((8 | k) << 12)));
+}
+
+__device__ __forceinline__ uint4 ldg_nc(const uint4* p) {
+  uint4 v;
+  asm volatile("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
+}
+
+// ---- shared-memory profile slices ------------------------------------------
+// Inter-task (packed) strip profile for T query rows, int8, replicated 8x so
+// that the 8 lanes of a quarter-warp read 16-byte rows of any residue codes
+// from 8 distinct bank groups (no bank conflicts for random residues):
+//   byte (c, half h, copy p, row r) at ((c * (T/16) + h) * 8 + p) * 16 + (r - 16h)
+template <int T>
+struct InterProfile {
+  static constexpr int BYTES = NCODES * 8 * T;
+};
+// Intra-task pass profile, int8: lane k's TI rows for code c at (c * 32 + k) * TI.
+template <int TI>
+struct IntraProfile {
+  static constexpr int BYTES = NCODES * 32 * TI;
+};
+
+template <int T, int TI>
+struct SliceBytes {
+  static constexpr int A = InterProfile<T>::BYTES, B = IntraProfile<TI>::BYTES;
+  static constexpr int BYTES = ((A > B ? A : B) + 15) / 16 * 16;
+};
+
+// ---- score output ------------------------------------------------------------
+__device__ __forceinline__ void emit_score(const DbView& db, const SearchParams* __restrict__ P,
+                                           int q, int s, int score) {
+  const int orig = db.perm[s];
+  if (orig >= 0) P->scores[(int64_t)q * db.n + orig] = score;
+}
+
+// ---- intra-task warp wavefront, int32 (Section II-B, intra-task) -----------
+template <int TI>
+__device__ void intra_item(const DbView& db, const SearchParams* __restrict__ P,
+                           const int8_t* __restrict__ sm, uint8_t* slice, int lane,
+                           int64_t warp_id, const Scratch& scr, int q, int s) {
+  const int n = db.clen[s];
+  const int m = P->qlen[q];
+  const uint8_t* __restrict__ d = db.cont + db.coff[s];
+  const uint8_t* __restrict__ qr = P->qres + P->qoff[q];
+  int2* hb = scr.intra_border + warp_id * scr.intra_stride;
+  const int go = P->go, ge = P->ge;
+  constexpr int ROWS = 32 * TI;
+  const int npass = (m + ROWS - 1) / ROWS;
+  int S = 0;
+  for (int p = 0; p < npass && n > 0; p++) {
+    __syncwarp();
+    // profile: this lane's TI rows for every code
+    {
+      const int i0 = p * ROWS + lane * TI;
+      int qc[TI];
+#pragma unroll
+      for (int r = 0; r < TI; r++) qc[r] = (i0 + r < m) ? (int)qr[i0 + r] : -1;
+      for (int c = 0; c < NCODES; c++) {
+        uint32_t wv[TI / 4];
+#pragma unroll
+        for (int w = 0; w < TI / 4; w++) {
+          uint32_t acc = 0;
+#pragma unroll
+          for (int b = 0; b < 4; b++) {
+            const int r = w * 4 + b;
+            const int v = qc[r] >= 0 ? (int)sm[qc[r] * NCODES + c] : PAD_SCORE;
+            acc |= ((uint32_t)(uint8_t)(int8_t)v) << (8 * b);
+          }
+          wv[w] = acc;
+        }
+        uint32_t* dst = (uint32_t*)(slice + (c * 32 + lane) * TI);
+#pragma unroll
+        for (int w = 0; w < TI / 4; w++) dst[w] = wv[w];
+      }
+    }
+    __syncwarp();
+    int Hp[TI], E[TI];
+#pragma unroll
+    for (int r = 0; r < TI; r++) {
+      Hp[r] = 0;    // H(i, 0)
+      E[r] = -go;   // E(i, 1)
+    }
+    int hdiag = 0, out_h = 0, out_f = -go;
+    const bool last_pass = (p == npass - 1);
+    const int steps = n + 31;
+    for (int t = 0; t < steps; t++) {
+      int in_h = __shfl_up_sync(FULL, out_h, 1);
+      int in_f = __shfl_up_sync(FULL, out_f, 1);
+      const int j = t - lane;
+      if (lane == 0) {
+        if (p > 0 && j < n) {
+          const int2 v = hb[j];
+          in_h = v.x;
+          in_f = v.y;
+        } else {
+          in_h = 0;     // H(0, j)
+          in_f = -go;   // F(1, j)
+        }
+      }
+      if (j >= 0 && j < n) {
+        const int c = d[j];
+        uint32_t pw[TI / 4];
+        if constexpr (TI == 8) {
+          const uint2 v = *(const uint2*)(slice + (c * 32 + lane) * TI);
+          pw[0] = v.x;
+          pw[1] = v.y;
+        } else {
+          const uint4 v = *(const uint4*)(slice + (c * 32 + lane) * TI);
+          pw[0] = v.x;
+          pw[1] = v.y;
+          pw[2] = v.z;
+          pw[3] = v.w;
+        }
+        int hd = hdiag;
+        hdiag = in_h;
+        int f = in_f;
+#pragma unroll
+        for (int r = 0; r < TI; r++) {
+          const int w = sext_byte(pw[r / 4], r & 3);
+          const int e = E[r];
+          const int h = __viaddmax_s32_relu(hd, w, max(e, f));
+          hd = Hp[r];
+          Hp[r] = h;
+          const int tt = h - go;
+          E[r] = __viaddmax_s32(e, -ge, tt);
+          f = __viaddmax_s32(f, -ge, tt);
+          S = max(S, h);
+        }
+        out_h = Hp[TI - 1];
+        out_f = f;
+        if (lane == 31 && !last_pass) hb[j] = make_int2(out_h, out_f);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) S = max(S, __shfl_xor_sync(FULL, S, o));
+  if (lane == 0) emit_score(db, P, q, s, S);
+}
+
+// ---- inter-task, packed 16-bit pairs (Section II-B, inter-task) ------------
+template <int T>
+__device__ void inter_item(const DbView& db, const SearchParams* __restrict__ P, SearchState* st,
+                           const int8_t* __restrict__ sm, uint8_t* slice, int lane,
+                           int64_t warp_id, const Scratch& scr, int q, int g) {
+  const int L = db.glen[g];  // multiple of CHUNK
+  const int m = P->qlen[q];
+  const uint8_t* __restrict__ qr = P->qres + P->qoff[q];
+  const uint4* __restrict__ res = (const uint4*)(db.inter + db.goff[g]) + lane;
+  uint4* bd = scr.inter_border + warp_id * scr.inter_stride_vec + lane;
+  const uint32_t GO2 = pack2(P->go), NGE2 = pack2(-P->ge), NGO2 = pack2(-P->go);
+  const int p16 = (lane & 7) * 16;
+  constexpr int HALVES = T / 16;
+  const int nstrips = L > 0 ? (m + T - 1) / T : 0;
+  uint32_t smax = 0;
+  for (int s = 0; s < nstrips; s++) {
+    __syncwarp();
+    if (lane < NCODES) {  // code c = lane: T bytes, written to all 8 copies
+      const int i0 = s * T;
+      uint32_t wv[T / 4];
+#pragma unroll
+      for (int w = 0; w < T / 4; w++) {
+        uint32_t acc = 0;
+#pragma unroll
+        for (int b = 0; b < 4; b++) {
+          const int i = i0 + w * 4 + b;
+          const int v = i < m ? (int)sm[(int)qr[i] * NCODES + lane] : PAD_SCORE;
+          acc |= ((uint32_t)(uint8_t)(int8_t)v) << (8 * b);
+        }
+        wv[w] = acc;
+      }
+#pragma unroll
+      for (int h = 0; h < HALVES; h++) {
+        const uint4 v = make_uint4(wv[4 * h], wv[4 * h + 1], wv[4 * h + 2], wv[4 * h + 3]);
+#pragma unroll
+        for (int p = 0; p < 8; p++)
+          *(uint4*)(slice + ((lane * HALVES + h) * 8 + p) * 16) = v;
+      }
+    }
+    __syncwarp();
+    uint32_t Hp[T], E[T];
+#pragma unroll
+    for (int r = 0; r < T; r++) {
+      Hp[r] = 0;     // H(i, 0)
+      E[r] = NGO2;   // E(i, 1)
+    }
+    uint32_t hdiag = 0;
+    const bool first = (s == 0), last = (s == nstrips - 1);
+    for (int c = 0; c < L / CHUNK; c++) {
+      const uint4 rr = ldg_nc(res + c * 32);
+#pragma unroll
+      for (int jp = 0; jp < CHUNK / 2; jp++) {
+        // border vector of columns 2jp, 2jp+1: (H, F, H, F) of the row above the strip
+        const uint4 b = first ? make_uint4(0u, NGO2, 0u, NGO2)  // H(0,j) = 0, F(1,j) = -Go
+                              : bd[(c * 4 + jp) * 32];
+        uint4 o;
+#pragma unroll
+        for (int jh = 0; jh < 2; jh++) {
+          const int jj = 2 * jp + jh;
+          const uint32_t wa = jj < 4 ? rr.x : rr.y;
+          const uint32_t wb = jj < 4 ? rr.z : rr.w;
+          const uint32_t ca = (wa >> (8 * (jj & 3))) & 0xffu;
+          const uint32_t cb = (wb >> (8 * (jj & 3))) & 0xffu;
+          uint4 va[HALVES], vb[HALVES];
+#pragma unroll
+          for (int h = 0; h < HALVES; h++) {
+            va[h] = *(const uint4*)(slice + (ca * HALVES + h) * 128 + p16);
+            vb[h] = *(const uint4*)(slice + (cb * HALVES + h) * 128 + p16);
+          }
+          const uint32_t htop = jh ? b.z : b.x;
+          uint32_t f = jh ? b.w : b.y;
+          uint32_t hd = hdiag;
+          hdiag = htop;
+          uint32_t hprev = 0;
+#pragma unroll
+          for (int r = 0; r < T; r++) {
+            const uint4& A = va[r / 16];
+            const uint4& B = vb[r / 16];
+            const int wq = (r / 4) & 3;
+            const uint32_t a32 = wq == 0 ? A.x : wq == 1 ? A.y : wq == 2 ? A.z : A.w;
+            const uint32_t b32 = wq == 0 ? B.x : wq == 1 ? B.y : wq == 2 ? B.z : B.w;
+            const uint32_t w = prmt(a32, b32, sext_pair_sel(r & 3));
+            const uint32_t e = E[r];
+            const uint32_t h = __viaddmax_s16x2_relu(hd, w, __vmaxs2(e, f));
+            hd = Hp[r];
+            Hp[r] = h;
+            const uint32_t t = __vsub2(h, GO2);
+            E[r] = __viaddmax_s16x2(e, NGE2, t);
+            f = __viaddmax_s16x2(f, NGE2, t);
+            if (r & 1)
+              smax = __vimax3_s16x2(smax, hprev, h);
+            else
+              hprev = h;
+          }
+          if (jh) {
+            o.z = Hp[T - 1];
+            o.w = f;
+          } else {
+            o.x = Hp[T - 1];
+            o.y = f;
+          }
+        }
+        if (!last) bd[(c * 4 + jp) * 32] = o;
+      }
+    }
+  }
+  // two scores per lane; a saturated one goes to the int32 recompute list
+  const int base = g * GROUP + 2 * lane;
+#pragma unroll
+  for (int half = 0; half < 2; half++) {
+    const int sidx = base + half;
+    const int orig = db.perm[sidx];
+    if (orig < 0) continue;
+    const int score = (int)(int16_t)(half ? (smax >> 16) : (smax & 0xffffu));
+    if (score >= P->sat_threshold) {
+      const unsigned long long k = atomicAdd(&st->n_flags, 1ull);
+      if ((int64_t)k < scr.flag_capacity) scr.flags[k] = make_int2(q, sidx);
+    } else {
+      P->scores[(int64_t)q * db.n + orig] = score;
+    }
+  }
+}
+
+// ---- the persistent kernel ----------------------------------------------------
+template <int T, int TI>
+__global__ void __launch_bounds__(256, (T == 16 ? 2 : 1))
+search_kernel(int mode, DbView db, const SearchParams* __restrict__ P, SearchState* st,
+              Scratch scr) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  int8_t* sm = (int8_t*)smem;
+  for (int i = threadIdx.x; i < NCODES * NCODES; i += blockDim.x) sm[i] = P->sm[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  uint8_t* slice = smem + MATRIX_SMEM + wib * SliceBytes<T, TI>::BYTES;
+  const int64_t warp_id = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+  const int nq = P->nq;
+  if (nq <= 0) return;
+  if (mode == 0) {
+    const int64_t n_intra = P->n_intra_items;
+    const int64_t total = n_intra + P->n_inter_items;
+    for (;;) {
+      unsigned long long it = 0;
+      if (lane == 0) it = atomicAdd(&st->work, 1ull);
+      it = __shfl_sync(FULL, it, 0);
+      if ((int64_t)it >= total) break;
+      if ((int64_t)it < n_intra) {
+        const int s = (int)((int64_t)it / nq);
+        const int q = P->qorder[(int64_t)it % nq];
+        intra_item<TI>(db, P, sm, slice, lane, warp_id, scr, q, s);
+      } else {
+        const int64_t k = (int64_t)it - n_intra;
+        const int g = P->g_first + (int)(k / nq);
+        const int q = P->qorder[k % nq];
+        inter_item<T>(db, P, st, sm, slice, lane, warp_id, scr, q, g);
+      }
+    }
+  } else {
+    const unsigned long long nf = *(volatile unsigned long long*)&st->n_flags;
+    const unsigned long long total =
+        nf < (unsigned long long)scr.flag_capacity ? nf : (unsigned long long)scr.flag_capacity;
+    for (;;) {
+      unsigned long long it = 0;
+      if (lane == 0) it = atomicAdd(&st->recompute, 1ull);
+      it = __shfl_sync(FULL, it, 0);
+      if (it >= total) break;
+      const int2 fl = scr.flags[it];
+      intra_item<TI>(db, P, sm, slice, lane, warp_id, scr, fl.x, fl.y);
+    }
+  }
+}
+
+typedef void (*SearchKernel)(int, DbView, const SearchParams*, SearchState*, Scratch);
+
+static SearchKernel pick_search(int rows, int intra_rows) {
+  if (rows == 16 && intra_rows == 8) return search_kernel<16, 8>;
+  if (rows == 16 && intra_rows == 16) return search_kernel<16, 16>;
+  if (rows == 32 && intra_rows == 8) return search_kernel<32, 8>;
+  if (rows == 32 && intra_rows == 16) return search_kernel<32, 16>;
+  return nullptr;
+}
+
+static int slice_bytes(int rows, int intra_rows) {
+  if (rows == 16 && intra_rows == 8) return SliceBytes<16, 8>::BYTES;
+  if (rows == 16 && intra_rows == 16) return SliceBytes<16, 16>::BYTES;
+  if (rows == 32 && intra_rows == 8) return SliceBytes<32, 8>::BYTES;
+  if (rows == 32 && intra_rows == 16) return SliceBytes<32, 16>::BYTES;
+  return 0;
+}
+
+size_t search_smem_bytes(int rows, int intra_rows, int warps) {
+  return (size_t)MATRIX_SMEM + (size_t)warps * slice_bytes(rows, intra_rows);
+}
+
+int search_blocks_per_sm(int rows, int intra_rows, int warps) {
+  SearchKernel k = pick_search(rows, intra_rows);
+  if (!k || warps < 1 || warps > 8) return 0;
+  const size_t smem = search_smem_bytes(rows, intra_rows, warps);
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return 0;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, warps * 32, smem) != cudaSuccess)
+    return 0;
+  return nb;
+}
+
+cudaError_t launch_search(const KernelConfig& kc, int mode, const DbView& db,
+                          const SearchParams* params, SearchState* state, const Scratch& scr,
+                          cudaStream_t stream) {
+  // the dynamic shared-memory attribute was set by search_blocks_per_sm when
+  // the plan was created; nothing here may be an unsafe call under capture
+  SearchKernel k = pick_search(kc.rows, kc.intra_rows);
+  if (!k) return cudaErrorInvalidValue;
+  k<<<kc.blocks, kc.warps * 32, kc.smem, stream>>>(mode, db, params, state, scr);
+  return cudaGetLastError();
+}
+
+// ---- plain int32 baseline: Algorithm 1, one launch per query ---------------
+constexpr int PT = 8;  // query rows per thread
+constexpr int NEG = -(1 << 28);
+
+__global__ void __launch_bounds__(GROUP)
+plain_kernel(DbView db, const SearchParams* __restrict__ P, int q, int2* border,
+             const int64_t* __restrict__ border_off) {
+  __shared__ int8_t sm[NCODES * NCODES];
+  __shared__ int prof[NCODES][PT];
+  for (int i = threadIdx.x; i < NCODES * NCODES; i += blockDim.x) sm[i] = P->sm[i];
+  const int k = threadIdx.x;  // subject slot in the group
+  const int m = P->qlen[q];
+  const uint8_t* __restrict__ qr = P->qres + P->qoff[q];
+  const int go = P->go, ge = P->ge;
+  int2* bd = border + border_off[blockIdx.x] + k;
+  __syncthreads();
+  for (int g = blockIdx.x; g < db.groups; g += gridDim.x) {
+    const int L = db.glen[g];
+    const uint2* __restrict__ res = (const uint2*)(db.inter + db.goff[g]) + k;
+    const int nstrips = L > 0 ? (m + PT - 1) / PT : 0;
+    int S = 0;
+    for (int s = 0; s < nstrips; s++) {
+      __syncthreads();
+      for (int i = threadIdx.x; i < NCODES * PT; i += blockDim.x) {
+        const int c = i / PT, r = i % PT, row = s * PT + r;
+        prof[c][r] = row < m ? (int)sm[(int)qr[row] * NCODES + c] : PAD_SCORE;
+      }
+      __syncthreads();
+      int Hl[PT], El[PT];
+#pragma unroll
+      for (int r = 0; r < PT; r++) {
+        Hl[r] = 0;
+        El[r] = NEG;
+      }
+      int hul = 0;
+      const bool last = (s == nstrips - 1);
+      for (int c = 0; c < L / CHUNK; c++) {
+        const uint2 rr = res[c * GROUP];
+#pragma unroll
+        for (int jj = 0; jj < CHUNK; jj++) {
+          const int cj = ((jj < 4 ? rr.x : rr.y) >> (8 * (jj & 3))) & 0xff;
+          int hu = 0, fu = NEG;  // H and F of the row above the strip
+          if (s > 0) {
+            const int2 v = bd[(c * CHUNK + jj) * GROUP];
+            hu = v.x;
+            fu = v.y;
+          }
+          int hd = hul;
+          hul = hu;
+#pragma unroll
+          for (int r = 0; r < PT; r++) {
+            // Algorithm 1: E, F, H, S
+            const int e = max(El[r] - ge, Hl[r] - go);
+            const int f = max(fu - ge, hu - go);
+            int h = hd + prof[cj][r];
+            h = max(h, e);
+            h = max(h, f);
+            h = max(h, 0);
+            S = max(h, S);
+            hd = Hl[r];
+            Hl[r] = h;
+            El[r] = e;
+            hu = h;
+            fu = f;
+          }
+          if (!last) bd[(c * CHUNK + jj) * GROUP] = make_int2(hu, fu);
+        }
+      }
+    }
+    const int orig = db.perm[g * GROUP + k];
+    if (orig >= 0) P->scores[(int64_t)q * db.n + orig] = S;
+  }
+}
+
+int plain_blocks_per_sm() {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, plain_kernel, GROUP, 0) != cudaSuccess)
+    return 0;
+  return nb;
+}
+
+cudaError_t launch_plain(int blocks, const DbView& db, const SearchParams* params, int query,
+                         int2* border, const int64_t* border_off, cudaStream_t stream) {
+  plain_kernel<<<blocks, GROUP, 0, stream>>>(db, params, query, border, border_off);
+  return cudaGetLastError();
+}
+
+}  // namespace swgb

@@ -1,0 +1,113 @@
+// swgb_internal.h -- types and helpers shared by the CUDA translation units
+// of libswgb.  Nothing here is part of the public ABI (include/swgb.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/swgb.h"
+
+namespace swgb {
+
+// ---- alphabet and layout constants ------------------------------------------
+constexpr int ALPHA = 24;        // BLOSUM62 symbols A R N D C Q E G H I L K M F P S T W Y V B Z X *
+constexpr int PAD_CODE = 24;     // trailing padding residue (never in user input)
+constexpr int NCODES = 25;       // ALPHA + PAD
+constexpr int PAD_SCORE = -64;   // SM against PAD: trailing cells scoring <= 0 leave S unchanged
+constexpr int GROUP = 64;        // subjects per inter-task group (32 lanes x 2 packed subjects)
+constexpr int CHUNK = 8;         // residues per subject per interleaved chunk
+constexpr int CHUNK_BYTES = GROUP * CHUNK;  // 512 bytes: one chunk of a whole group
+constexpr int S16_LIMIT = 32767;
+
+// ---- error reporting ----------------------------------------------------------
+sw_status sw_set_error(sw_status st, const char* fmt, ...);
+sw_status sw_set_cuda_error(cudaError_t err, const char* where);
+void sw_clear_error();
+
+#define CUDA_TRY(call)                                                       \
+  do {                                                                       \
+    cudaError_t _e = (call);                                                 \
+    if (_e != cudaSuccess) return ::swgb::sw_set_cuda_error(_e, #call);      \
+  } while (0)
+
+// ---- device-resident database view (passed by value to kernels) -------------
+struct DbView {
+  const uint8_t* inter;  // interleaved groups: [group][chunk][lane][2 subjects][8 residues]
+  const int64_t* goff;   // [G] byte offset of each group in `inter`
+  const int32_t* glen;   // [G] group length padded to a multiple of CHUNK
+  const uint8_t* cont;   // all subjects, sorted by length (descending), contiguous
+  const int64_t* coff;   // [N] offset of sorted subject s in `cont`
+  const int32_t* clen;   // [N] length of sorted subject s
+  const int32_t* perm;   // [G * GROUP] sorted index -> caller index, -1 for padding slots
+  int64_t n;             // subjects
+  int32_t groups;        // G
+  int32_t max_len;       // longest subject
+};
+
+// ---- per-search parameters, read by the kernels from device memory ----------
+// Kept in device memory (not kernel arguments) so that one captured CUDA graph
+// serves every batch: a new search only rewrites this block.
+struct SearchParams {
+  const uint8_t* qres;    // concatenated query codes
+  const int64_t* qoff;    // [nq]
+  const int32_t* qlen;    // [nq]
+  const int32_t* qorder;  // [nq] query indices, longest first
+  int32_t* scores;        // [nq x N] caller order
+  int64_t n_intra_items;  // n_long x nq  (int32 intra-task items)
+  int64_t n_inter_items;  // inter groups x nq  (packed inter-task items)
+  int32_t nq;
+  int32_t n_long;         // sorted subjects [0, n_long) go to the intra-task kernel
+  int32_t g_first;        // first inter-task group (n_long / GROUP)
+  int32_t go;             // Go = gap_open + gap_extend  (Eq. 2-3)
+  int32_t ge;             // Ge = gap_extend
+  int32_t sat_threshold;  // a 16-bit score >= this is recomputed in int32
+  int8_t sm[NCODES * NCODES];  // SM(query code, subject code), PAD row/column = PAD_SCORE
+};
+
+// ---- per-search device state (zeroed before each search) --------------------
+struct SearchState {
+  unsigned long long work;       // next work item (search kernel)
+  unsigned long long n_flags;    // saturated pairs appended to the flag list
+  unsigned long long recompute;  // next flag item (recompute kernel)
+  unsigned int status;           // reserved: error bits raised on the device
+  unsigned int pad;
+};
+
+// ---- scratch handed to the kernels --------------------------------------------
+struct Scratch {
+  uint4* inter_border;        // per warp: [chunk][4][lane] uint4 (H,F words of 2 columns)
+  int64_t inter_stride_vec;   // uint4 per warp
+  int2* intra_border;         // per warp: [column] (H, F) int32
+  int64_t intra_stride;       // int2 per warp
+  int2* flags;                // saturated pairs: (query index, sorted subject index)
+  int64_t flag_capacity;
+};
+
+// ---- kernel launchers (search_kernels.cu) -------------------------------------
+struct KernelConfig {
+  int rows;        // packed rows per thread (16 or 32)
+  int intra_rows;  // int32 rows per lane (8 or 16)
+  int warps;       // warps per block
+  int blocks;      // grid size
+  size_t smem;     // dynamic shared memory per block
+};
+
+// Shared-memory bytes a block needs for a configuration.
+size_t search_smem_bytes(int rows, int intra_rows, int warps);
+// Resident blocks per SM for a configuration (0 if it cannot launch).
+int search_blocks_per_sm(int rows, int intra_rows, int warps);
+// mode 0: search (intra items, then inter items); mode 1: recompute flagged pairs.
+cudaError_t launch_search(const KernelConfig& kc, int mode, const DbView& db,
+                          const SearchParams* params, SearchState* state, const Scratch& scr,
+                          cudaStream_t stream);
+
+// Plain int32 baseline (Algorithm 1 per cell), one query per launch.
+int plain_blocks_per_sm();
+cudaError_t launch_plain(int blocks, const DbView& db, const SearchParams* params, int query,
+                         int2* border, const int64_t* border_off, cudaStream_t stream);
+
+// Integer-pipe microbenchmark (intpeak.cu).
+int intpeak_run(int op, int blocks_per_sm, int threads, int iters, double* lane_ops_per_clk_sm,
+                double* clock_mhz, double* seconds);
+
+}  // namespace swgb

@@ -1,0 +1,309 @@
+"""Thin ctypes binding of libswgb (include/swgb.h): argument marshalling only.
+
+Every step of a search runs in the library's CUDA kernels.  There is no CPU
+fallback: if ``_build/libswgb.so`` is missing, loading raises.  Arrays may be
+numpy arrays (host) or torch tensors (host or CUDA); a torch stream or a raw
+``cudaStream_t`` integer selects the stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libswgb.so")
+
+SW_OK, SW_EINVAL, SW_ENOMEM, SW_ECUDA, SW_ETIMEDOUT, SW_EBUSY = range(6)
+_STATUS = {1: "SW_EINVAL", 2: "SW_ENOMEM", 3: "SW_ECUDA", 4: "SW_ETIMEDOUT", 5: "SW_EBUSY"}
+ALPHABET = "ARNDCQEGHILKMFPSTWYVBZX*"
+
+#: intpeak op codes (sw_intpeak)
+INTPEAK_OPS = ["iadd", "imax", "viaddmax_s32", "viaddmax_s16x2", "viaddmax_s16x2_relu",
+               "vimax3_s16x2", "vmaxs2", "vsub2", "vaddss2", "prmt", "cell_s16x2",
+               "cell_s16x2_prmt", "cell_i32"]
+
+
+class SwError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("rows_per_thread", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
+                ("long_cutoff", ctypes.c_int32), ("intra_rows", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32), ("force_int32", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("cells", ctypes.c_int64), ("inter_items", ctypes.c_int64),
+                ("intra_items", ctypes.c_int64), ("recomputed_pairs", ctypes.c_int64),
+                ("timed_out", ctypes.c_int32), ("kernels_launched", ctypes.c_int32),
+                ("search_ms", ctypes.c_float), ("recompute_ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Loads libswgb.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libswgb.so is missing ({LIB_PATH}); build it with "
+                               "`python -m paper_2309_09609_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        sig = {
+            "sw_last_error": (ctypes.c_char_p, []),
+            "sw_encode": (i32, [P, i64, P]),
+            "sw_default_matrix": (None, [P]),
+            "sw_db_create": (i32, [P, P, i64, ctypes.c_int, ctypes.POINTER(P)]),
+            "sw_db_destroy": (None, [P]),
+            "sw_db_subjects": (i64, [P]),
+            "sw_db_residues": (i64, [P]),
+            "sw_db_max_length": (i32, [P]),
+            "sw_options_default": (None, [ctypes.POINTER(Options)]),
+            "sw_plan_create": (i32, [P, i32, i64, ctypes.POINTER(Options), ctypes.POINTER(P)]),
+            "sw_plan_destroy": (None, [P]),
+            "sw_plan_search": (i32, [P, P, P, i32, i32, i32, P, P, P]),
+            "sw_plan_search_async": (i32, [P, P, P, i32, i32, i32, P, P, P]),
+            "sw_plan_wait": (i32, [P, i32]),
+            "sw_plan_stats": (i32, [P, ctypes.POINTER(Stats)]),
+            "sw_search": (i32, [P, P, P, i32, i32, i32, P, P, P]),
+            "sw_search_plain": (i32, [P, P, P, i32, i32, i32, P, P, P]),
+            "sw_intpeak": (i32, [i32, i32, i32, i32, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+        return L
+
+
+def _check(status: int):
+    if status != SW_OK:
+        raise SwError(status, lib().sw_last_error().decode(errors="replace"))
+
+
+def last_error() -> str:
+    return lib().sw_last_error().decode(errors="replace")
+
+
+def _ptr(x):
+    """Raw pointer of a numpy array or torch tensor (kept alive by the caller)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous(), "tensor must be contiguous"
+        return ctypes.c_void_p(x.data_ptr())
+    assert isinstance(x, np.ndarray) and x.flags.c_contiguous, "need a contiguous numpy array"
+    return ctypes.c_void_p(x.ctypes.data)
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _u8(x):
+    if hasattr(x, "data_ptr"):
+        return x
+    return np.ascontiguousarray(x, dtype=np.uint8)
+
+
+def _i32(x):
+    if hasattr(x, "data_ptr"):
+        return x
+    return np.ascontiguousarray(x, dtype=np.int32)
+
+
+def _matrix(m):
+    if m is None:
+        return None
+    if hasattr(m, "data_ptr"):
+        return m
+    m = np.ascontiguousarray(m)
+    assert m.size == 576, "matrix must be 24 x 24"
+    assert m.min() >= -128 and m.max() <= 127, "matrix entries must fit int8"
+    return np.ascontiguousarray(m.astype(np.int8).reshape(576))
+
+
+def encode(text: str) -> np.ndarray:
+    b = text.encode("latin-1")
+    out = np.empty(len(b), dtype=np.uint8)
+    src = np.frombuffer(b, dtype=np.uint8) if b else np.zeros(1, np.uint8)
+    _check(lib().sw_encode(_ptr(src), len(b), _ptr(out) if len(b) else None))
+    return out
+
+
+def default_matrix() -> np.ndarray:
+    out = np.zeros(576, dtype=np.int8)
+    lib().sw_default_matrix(_ptr(out))
+    return out.reshape(24, 24)
+
+
+def options(**kw) -> Options:
+    o = Options()
+    lib().sw_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, int(v))
+    return o
+
+
+def _query_args(queries, q_lengths):
+    q = _u8(queries)
+    ql = _i32(q_lengths)
+    n = int(ql.shape[0]) if hasattr(ql, "shape") else len(ql)
+    if (hasattr(q, "numel") and q.numel() == 0) or (isinstance(q, np.ndarray) and q.size == 0):
+        q = np.zeros(1, np.uint8)
+    return q, ql, n
+
+
+class Database:
+    """A protein database resident on one GPU (sw_db_create)."""
+
+    def __init__(self, residues, lengths, device: int = 0):
+        res = _u8(residues)
+        lens = _i32(lengths)
+        n = int(lens.shape[0])
+        if isinstance(res, np.ndarray) and res.size == 0:
+            res = np.zeros(1, np.uint8)
+        h = ctypes.c_void_p()
+        _check(lib().sw_db_create(_ptr(res), _ptr(lens) if n else None, n, device, ctypes.byref(h)))
+        self._h = h
+        self.device = device
+        self.n = n
+
+    @classmethod
+    def from_seqset(cls, ss, device: int = 0):
+        return cls(ss.res, ss.lens, device)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sw_db_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def residues(self) -> int:
+        return int(lib().sw_db_residues(self._h))
+
+    @property
+    def max_length(self) -> int:
+        return int(lib().sw_db_max_length(self._h))
+
+    def _out(self, nq, out):
+        if out is None:
+            out = np.empty((nq, self.n), dtype=np.int32)
+        return out
+
+    def search(self, queries, q_lengths, gap_open=10, gap_extend=2, matrix=None, out=None,
+               stream=None):
+        """One-shot exact search (sw_search); returns scores [nq, n_subjects]."""
+        q, ql, nq = _query_args(queries, q_lengths)
+        out = self._out(nq, out)
+        m = _matrix(matrix)
+        _check(lib().sw_search(self._h, _ptr(q), _ptr(ql), nq, gap_open, gap_extend, _ptr(m),
+                               _ptr(out), _stream(stream)))
+        return out
+
+    def search_plain(self, queries, q_lengths, gap_open=10, gap_extend=2, matrix=None, out=None,
+                     stream=None):
+        """The int32 one-query-per-launch baseline (sw_search_plain)."""
+        q, ql, nq = _query_args(queries, q_lengths)
+        out = self._out(nq, out)
+        m = _matrix(matrix)
+        _check(lib().sw_search_plain(self._h, _ptr(q), _ptr(ql), nq, gap_open, gap_extend,
+                                     _ptr(m), _ptr(out), _stream(stream)))
+        return out
+
+    def plan(self, max_queries: int, max_query_residues: int, **opts) -> "Plan":
+        return Plan(self, max_queries, max_query_residues, options(**opts))
+
+
+class Plan:
+    """A reusable search context (sw_plan_create): buffers + CUDA graph."""
+
+    def __init__(self, db: Database, max_queries: int, max_query_residues: int, opts=None):
+        h = ctypes.c_void_p()
+        _check(lib().sw_plan_create(db._h, int(max_queries), int(max_query_residues),
+                                    ctypes.byref(opts) if opts is not None else None,
+                                    ctypes.byref(h)))
+        self._h = h
+        self.db = db
+        self.max_queries = int(max_queries)
+        self.max_query_residues = int(max_query_residues)
+        self._keep = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sw_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def search(self, queries, q_lengths, gap_open=10, gap_extend=2, matrix=None, out=None,
+               stream=None):
+        q, ql, nq = _query_args(queries, q_lengths)
+        if out is None:
+            out = np.empty((nq, self.db.n), dtype=np.int32)
+        m = _matrix(matrix)
+        _check(lib().sw_plan_search(self._h, _ptr(q), _ptr(ql), nq, gap_open, gap_extend,
+                                    _ptr(m), _ptr(out), _stream(stream)))
+        return out
+
+    def search_async(self, queries, q_lengths, out, gap_open=10, gap_extend=2, matrix=None,
+                     stream=None):
+        """Queues a search; `out` must be device memory (e.g. a CUDA tensor)."""
+        q, ql, nq = _query_args(queries, q_lengths)
+        m = _matrix(matrix)
+        self._keep = (q, ql, m, out)
+        _check(lib().sw_plan_search_async(self._h, _ptr(q), _ptr(ql), nq, gap_open, gap_extend,
+                                          _ptr(m), _ptr(out), _stream(stream)))
+
+    def wait(self, timeout_ms: int = -1) -> bool:
+        """True when done; False if still running after timeout_ms."""
+        st = lib().sw_plan_wait(self._h, int(timeout_ms))
+        if st == SW_ETIMEDOUT:
+            return False
+        _check(st)
+        self._keep = None
+        return True
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().sw_plan_stats(self._h, ctypes.byref(s)))
+        return s.as_dict()
+
+
+def intpeak(op, blocks_per_sm: int = 8, threads: int = 256, iters: int = 20000):
+    """Integer-pipe microbenchmark: (lane-ops per SM clock, SM MHz, seconds)."""
+    code = INTPEAK_OPS.index(op) if isinstance(op, str) else int(op)
+    out = np.zeros(3, dtype=np.float64)
+    _check(lib().sw_intpeak(code, blocks_per_sm, threads, iters, _ptr(out)))
+    return float(out[0]), float(out[1]), float(out[2])

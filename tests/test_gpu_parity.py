@@ -1,0 +1,228 @@
+"""CUDA path vs the CPU oracle, bit-exact on every pair (integer scores).
+
+Each case runs the library's paths through the C ABI -- the one-shot search,
+a plan replaying its CUDA graph, and the plain int32 baseline -- and compares
+every score with the oracle (Eq. 1-3).  Sizes span several tiles and ragged
+tails: query lengths around the 16/32-row strips and the 256/512-row intra
+passes, subject lengths around the 8-residue chunks and the 64-subject groups.
+"""
+import numpy as np
+import pytest
+
+from helpers import concat, from_text, oracle_all, oracle_pairs, rand_matrix, seqset
+from paper_2309_09609_gb300 import build as nvbuild
+from paper_2309_09609_gb300 import swgb, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    nvbuild.build()
+    swgb.lib()
+
+
+def all_paths(q, db, go=10, ge=2, matrix=None, plain=True, **opts):
+    d = swgb.Database.from_seqset(db)
+    res = {"search": d.search(q.res, q.lens, go, ge, matrix)}
+    p = d.plan(max(len(q), 1), max(q.total, 1), **opts)
+    res["plan"] = p.search(q.res, q.lens, go, ge, matrix)
+    res["plan_replay"] = p.search(q.res, q.lens, go, ge, matrix)
+    if plain:
+        res["plain"] = d.search_plain(q.res, q.lens, go, ge, matrix)
+    return res, p.stats()
+
+
+def assert_exact(res, want):
+    for name, got in res.items():
+        assert got.shape == want.shape, name
+        bad = np.argwhere(got != want)
+        assert bad.size == 0, f"{name}: {len(bad)} pairs differ, first {bad[:5].tolist()} " \
+                              f"got {got[tuple(bad[0])]} want {want[tuple(bad[0])]}"
+
+
+def test_plain_small_workload():
+    w = synth.plain_small(0)
+    res, st = all_paths(w.queries, w.db)
+    assert_exact(res, oracle_all(w.queries, w.db))
+    assert st["cells"] == w.cells
+
+
+@pytest.mark.parametrize("rows", [16, 32])
+@pytest.mark.parametrize("gaps", [(10, 2), (5, 1), (0, 1), (11, 1), (0, 0)])
+def test_ragged_tiles(rows, gaps):
+    rng = np.random.default_rng(rows * 100 + gaps[0] * 7 + gaps[1])
+    db = seqset(rng, list(range(0, 10)) + list(rng.integers(0, 300, size=503)))
+    q = seqset(rng, [0, 1, 5, 15, 16, 17, 31, 32, 33, 250])
+    res, _ = all_paths(q, db, *gaps, rows_per_thread=rows)
+    assert_exact(res, oracle_all(q, db, *gaps))
+
+
+def test_full_alphabet_and_asymmetric_matrix():
+    rng = np.random.default_rng(3)
+    m = rand_matrix(rng, -6, 9, symmetric=False)
+    db = seqset(rng, rng.integers(1, 200, size=300), alpha=24)
+    q = seqset(rng, [1, 7, 40, 77, 130], alpha=24)
+    res, _ = all_paths(q, db, 6, 2, m)
+    assert_exact(res, oracle_all(q, db, 6, 2, m.astype(np.int32)))
+
+
+@pytest.mark.parametrize("intra_rows", [8, 16])
+def test_long_subjects_intra_task(intra_rows):
+    rng = np.random.default_rng(4 + intra_rows)
+    # 150 long subjects (intra-task groups) and 130 of length <= 60 (inter-task groups)
+    db = seqset(rng, list(rng.integers(1, 1500, size=150)) + [64, 65, 63, 1] +
+                list(rng.integers(1, 61, size=130)))
+    q = seqset(rng, [1, 31, 255, 256, 257, 300, 513, 700])
+    res, st = all_paths(q, db, long_cutoff=64, intra_rows=intra_rows)
+    assert st["intra_items"] > 0 and st["inter_items"] > 0
+    assert_exact(res, oracle_all(q, db))
+
+
+def test_force_int32_everywhere():
+    rng = np.random.default_rng(5)
+    db = seqset(rng, rng.integers(0, 400, size=200))
+    q = seqset(rng, [3, 100, 333])
+    res, st = all_paths(q, db, force_int32=1)
+    assert st["inter_items"] == 0
+    assert_exact(res, oracle_all(q, db))
+
+
+def test_saturation_is_recomputed_exactly():
+    # runs of W score 11 each: 2977 -> 32747 stays in 16 bits, 2978 -> 32758
+    # reaches the recompute threshold 32767 - 11, 3100 overflows
+    rng = np.random.default_rng(6)
+    w = lambda k: "W" * k
+    q = from_text(w(3100), w(2978) + "A" * 50, "HEAGAWGHEE")
+    subj = from_text(w(2977), w(2978), w(2990), w(3000) + "K" * 20, "PAWHEAE")
+    filler = seqset(rng, rng.integers(10, 300, size=100))
+    db = concat(subj, filler)
+    want = oracle_all(q, db)
+    assert want.max() > 32767
+    res, st = all_paths(q, db, long_cutoff=4000)  # every group on the packed path
+    assert st["recomputed_pairs"] >= 6
+    assert_exact(res, want)
+
+
+def test_saturation_with_large_matrix_entries():
+    rng = np.random.default_rng(7)
+    m = rand_matrix(rng, -20, 10)
+    np.fill_diagonal(m, 100)
+    base = seqset(rng, [400])
+    q = concat(base, seqset(rng, [50, 200]))
+    db = concat(base, base, seqset(rng, rng.integers(5, 500, size=130)))
+    want = oracle_all(q, db, 10, 2, m.astype(np.int32))
+    assert want.max() > 32767
+    res, st = all_paths(q, db, 10, 2, m)
+    assert st["recomputed_pairs"] >= 2
+    assert_exact(res, want)
+
+
+def test_huge_gap_penalties_take_the_int32_path():
+    rng = np.random.default_rng(8)
+    db = seqset(rng, rng.integers(0, 120, size=90))
+    q = seqset(rng, [10, 64, 100])
+    res, st = all_paths(q, db, 100000, 100000)
+    assert st["inter_items"] == 0
+    assert_exact(res, oracle_all(q, db, 100000, 100000))
+
+
+def test_subject_permutation_permutes_columns():
+    rng = np.random.default_rng(9)
+    db = seqset(rng, rng.integers(0, 250, size=200))
+    q = seqset(rng, [20, 90])
+    perm = rng.permutation(len(db))
+    db2 = db.subset(perm)
+    d1, d2 = swgb.Database.from_seqset(db), swgb.Database.from_seqset(db2)
+    a = d1.search(q.res, q.lens)
+    b = d2.search(q.res, q.lens)
+    assert (a[:, perm] == b).all()
+
+
+def test_equal_lengths_and_cutoff_edges():
+    rng = np.random.default_rng(10)
+    db = concat(seqset(rng, [100] * 64), seqset(rng, [199, 200, 201, 8, 7, 9, 16]))
+    q = seqset(rng, [17, 64])
+    res, st = all_paths(q, db, long_cutoff=200)
+    assert_exact(res, oracle_all(q, db))
+
+
+def test_device_tensors_in_and_out():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(11)
+    db = seqset(rng, rng.integers(1, 300, size=150))
+    q = seqset(rng, [33, 120])
+    d = swgb.Database.from_seqset(db)
+    qt = torch.from_numpy(q.res).cuda()
+    lt = torch.from_numpy(q.lens).cuda()
+    out = torch.empty((len(q), len(db)), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    d.search(qt, lt, 10, 2, out=out, stream=stream)
+    p = d.plan(4, 1000)
+    out2 = torch.empty_like(out)
+    p.search(qt, lt, 10, 2, out=out2, stream=stream)
+    want = oracle_all(q, db)
+    assert (out.cpu().numpy() == want).all()
+    assert (out2.cpu().numpy() == want).all()
+
+
+def test_plan_reuse_across_batches_and_scoring():
+    rng = np.random.default_rng(12)
+    db = seqset(rng, list(rng.integers(1, 600, size=300)) + [900, 1300])
+    d = swgb.Database.from_seqset(db)
+    p = d.plan(16, 8000, long_cutoff=800)
+    m = rand_matrix(rng, -4, 6, symmetric=True)
+    batches = [
+        (seqset(rng, [100, 7, 300]), 10, 2, None),
+        (seqset(rng, [45] * 9 + [512]), 3, 1, m),
+        (seqset(rng, [1]), 10, 2, None),
+        (seqset(rng, [0, 0]), 10, 2, None),
+    ]
+    for q, go, ge, mm in batches:
+        got = p.search(q.res, q.lens, go, ge, mm)
+        want = oracle_all(q, db, go, ge, None if mm is None else mm.astype(np.int32))
+        assert (got == want).all()
+
+
+def test_async_search_and_bounded_wait():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(13)
+    db = seqset(rng, rng.integers(1, 500, size=4000))
+    q = seqset(rng, [500, 800])
+    d = swgb.Database.from_seqset(db)
+    p = d.plan(2, 2000)
+    out = torch.empty((2, len(db)), dtype=torch.int32, device="cuda")
+    p.search_async(q.res, q.lens, out)
+    p.wait(0)                      # a poll returns at once, finished or not
+    assert p.wait(-1) is True
+    assert p.wait(0) is True       # nothing in flight any more
+    want = oracle_all(q, db)
+    assert (out.cpu().numpy() == want).all()
+
+
+def test_empty_inputs():
+    rng = np.random.default_rng(14)
+    db = seqset(rng, [0, 0, 5])
+    d = swgb.Database.from_seqset(db)
+    q = seqset(rng, [0, 4])
+    assert (d.search(q.res, q.lens) == oracle_all(q, db)).all()
+    assert d.search(np.zeros(0, np.uint8), np.zeros(0, np.int32)).shape == (0, 3)
+    e = swgb.Database(np.zeros(0, np.uint8), np.zeros(0, np.int32))
+    assert e.search(q.res, q.lens).shape == (2, 0)
+
+
+def test_invalid_query_is_rejected_and_context_survives():
+    rng = np.random.default_rng(15)
+    db = seqset(rng, [10, 20])
+    d = swgb.Database.from_seqset(db)
+    with pytest.raises(swgb.SwError) as e:
+        d.search(np.array([1, 2, 99], np.uint8), np.array([3], np.int32))
+    assert e.value.status == swgb.SW_EINVAL
+    with pytest.raises(swgb.SwError):
+        d.search(np.array([1, 2], np.uint8), np.array([2], np.int32), -1, 2)
+    p = d.plan(1, 4)
+    with pytest.raises(swgb.SwError) as e:
+        p.search(np.zeros(10, np.uint8), np.array([10], np.int32))
+    assert e.value.status == swgb.SW_EBUSY
+    q = seqset(rng, [5])
+    assert (d.search(q.res, q.lens) == oracle_all(q, db)).all()
