@@ -55,15 +55,30 @@ def parse():
     ap.add_argument("--warps", type=int, default=None)
     ap.add_argument("--cpu-sample", type=float, default=0.01,
                     help="fraction of subjects the CPU oracle baseline searches")
+    ap.add_argument("--subjects", type=int, default=None,
+                    help="shrink the database (profiling / small cases)")
+    ap.add_argument("--queries", type=int, default=None, help="keep only the first N queries")
+    ap.add_argument("--serve", type=int, default=200,
+                    help="serving leg: arrivals replayed against the resident DB (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=50.0, help="Poisson arrival rate (1/s)")
+    ap.add_argument("--tune", action="store_true",
+                    help="pick the tile shape with the autotuner before timing")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
 
 
-def make_workload(name, seed):
+def make_workload(name, seed, subjects=None, queries=None):
     from paper_2309_09609_gb300 import synth
-    return {"paper-search": synth.paper_search, "plain-small": synth.plain_small,
-            "batched-uneven": synth.batched_uneven, "long": synth.long_sequences}[name](seed)
+    kw = {}
+    if subjects and name in ("paper-search", "batched-uneven", "long"):
+        kw["n_subjects"] = subjects
+    w = {"paper-search": synth.paper_search, "plain-small": synth.plain_small,
+         "batched-uneven": synth.batched_uneven, "long": synth.long_sequences}[name](seed, **kw)
+    if queries and queries < len(w.queries):
+        w.queries = w.queries.subset(range(queries))
+        w.name += f" (first {queries} queries)"
+    return w
 
 
 class ClockSampler:
@@ -169,7 +184,7 @@ def run_reference(args):
         return
     import oracle
     oracle.build()
-    w = make_workload(args.workload, args.seed)
+    w = make_workload(args.workload, args.seed, args.subjects, args.queries)
     frac = min(args.cpu_sample, 0.002) if args.workload == "paper-search" else args.cpu_sample
     sub = oracle_sample(w, frac)
     cores = os.cpu_count() or 1
@@ -194,6 +209,33 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_serving(d, db, args, opts, w):
+    """Replays a Poisson trace (lognormal query lengths, mean 400) against the
+    resident database through the continuous-batching server."""
+    from paper_2309_09609_gb300 import serve, synth
+    trace = synth.serving_trace(seed=args.seed, n=args.serve, rate=args.serve_rate)
+    srv = serve.Server(d, slots=4, max_batch=16, max_batch_residues=65536,
+                       gap_open=w.gap_open, gap_extend=w.gap_extend, **opts)
+    t0 = time.perf_counter()
+    try:
+        futs = serve.replay(srv, trace)
+    finally:
+        srv.close()
+    wall = time.perf_counter() - t0
+    rep = srv.report(wall)
+    # a few requests recomputed alone must equal their rows from the mix
+    check = np.linspace(0, len(trace.queries) - 1, 4).astype(int)
+    same = all((d.search(trace.queries.seq(int(i)), np.array([trace.queries.lens[i]], np.int32),
+                         w.gap_open, w.gap_extend)[0] == futs[int(i)].result()).all() for i in check)
+    offered = args.serve_rate * float(trace.queries.lens.mean()) * db.total / 1e9
+    return {"arrivals": len(trace.queries), "rate_per_s": args.serve_rate,
+            "p50_ms": round(rep["p50_ms"], 2), "p99_ms": round(rep["p99_ms"], 2),
+            "gcups": round(rep["gcups"], 1), "offered_gcups": round(offered, 1),
+            "batches": rep["batches"], "mean_batch": round(rep["mean_batch"], 2),
+            "max_concurrent_batches": rep["max_concurrent_batches"], "slots": 4,
+            "wall_s": round(wall, 2), "alone_equals_mixed": bool(same)}
+
+
 def run_native(args):
     import torch
     rank, world, local, dist = dist_setup(args)
@@ -203,7 +245,7 @@ def run_native(args):
     __graft_entry__.build()
     from paper_2309_09609_gb300 import swgb
 
-    w = make_workload(args.workload, args.seed)
+    w = make_workload(args.workload, args.seed, args.subjects, args.queries)
     q, db = w.queries, w.db
     nq, N = len(q), len(db)
     cells = w.cells
@@ -217,6 +259,14 @@ def run_native(args):
         opts["long_cutoff"] = args.cutoff
     if args.warps:
         opts["warps_per_block"] = args.warps
+    tuned = None
+    if args.tune:
+        from paper_2309_09609_gb300 import tune
+        t0 = time.perf_counter()
+        tuned = tune.tune(d, q, w.gap_open, w.gap_extend, cache=None)
+        opts.update(tuned["options"])
+        tuned = {"options": tuned["options"], "candidates": len(tuned["timings"]),
+                 "seconds": round(time.perf_counter() - t0, 2)}
     plan = d.plan(nq, q.total, **opts)
     stream = torch.cuda.Stream(device=device)
     q_dev = torch.from_numpy(q.res).to(device)
@@ -271,6 +321,7 @@ def run_native(args):
               "latency_ms": {"p50": round(float(np.percentile(step_ms, 50)), 3),
                              "p99": round(float(np.percentile(step_ms, 99)), 3)},
               "recomputed_pairs": stats["recomputed_pairs"],
+              "autotuned": tuned,
               "db_create_s": round(db_create_s, 3),
               "gpu_launches": stats["kernels_launched"] * args.steps,
               "clocks": clocks}
@@ -323,6 +374,10 @@ def run_native(args):
     result["e2e"] = {"value": round(world * cells / e2e_s / 1e9, 2), "unit": "GCUPS",
                      "h2d_bytes_per_step": int(q.total + 4 * nq),
                      "d2h_bytes_per_step": int(4 * nq * N), "ms_per_step": round(1e3 * e2e_s, 3)}
+
+    # serving: the same resident DB, Poisson arrivals, continuous batching
+    if args.serve > 0 and args.workload == "paper-search" and rank == 0 and world == 1:
+        result["serving"] = run_serving(d, db, args, opts, w)
 
     # CPU oracle on a bounded sample (rank 0, N = 1): baseline and parity check
     if rank == 0 and world == 1 and not args.no_cpu:

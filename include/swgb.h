@@ -174,7 +174,8 @@ sw_status sw_search_plain(sw_db* db, const uint8_t* queries, const int32_t* q_le
  * measured instead of looked up).  op selects an instruction kind (0 iadd,
  * 1 imax, 2 viaddmax_s32, 3 viaddmax_s16x2, 4 viaddmax_s16x2_relu,
  * 5 vimax3_s16x2, 6 vmaxs2, 7 vsub2, 8 vaddss2, 9 prmt, 10 packed cell pair,
- * 11 packed cell pair + prmt, 12 int32 cell); results (host memory):
+ * 11 packed cell pair + prmt, 12 int32 cell, 13 imad, 14 the biased packed
+ * cell pair of the search kernel); results (host memory):
  * out[0] lane-operations per SM clock, out[1] SM clock in MHz, out[2] seconds. */
 sw_status sw_intpeak(int32_t op, int32_t blocks_per_sm, int32_t threads, int32_t iters,
                      double* out);

@@ -99,9 +99,9 @@ extern "C" void sw_default_matrix(int8_t* out) {
 
 extern "C" void sw_options_default(sw_options* opt) {
   if (!opt) return;
-  opt->rows_per_thread = 32;
+  opt->rows_per_thread = 16;
   opt->warps_per_block = 8;
-  opt->long_cutoff = 3000;
+  opt->long_cutoff = 7000;
   opt->intra_rows = 8;
   opt->use_graph = 1;
   opt->force_int32 = 0;
@@ -366,6 +366,7 @@ static sw_status fill_scoring(SearchParams& P, int32_t gap_open, int32_t gap_ext
   P.go = gap_open + gap_extend;
   P.ge = gap_extend;
   P.sat_threshold = S16_LIMIT - maxsm;
+  P.one = 1;
   *packed_ok = (P.go + P.ge) <= kPackedMaxGap;
   return SW_OK;
 }
@@ -524,20 +525,26 @@ extern "C" void sw_plan_destroy(sw_plan* plan) {
 
 // The device work of one search: reset counters, persistent search, recompute.
 // Events around the two kernels give their device time on the launching
-// stream (inside a captured graph they become event-record nodes).
-// (cudaEventRecordExternal makes them real event-record nodes under capture).
-static cudaError_t enqueue_kernels(sw_plan* p, cudaStream_t s) {
+// stream.  Under stream capture an event record only orders the capture
+// unless it carries cudaEventRecordExternal, which makes it a real
+// event-record node of the graph; outside capture that flag is illegal.
+static cudaError_t record(cudaEvent_t ev, cudaStream_t s, bool capturing) {
+  return capturing ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal)
+                   : cudaEventRecord(ev, s);
+}
+
+static cudaError_t enqueue_kernels(sw_plan* p, cudaStream_t s, bool capturing) {
   cudaError_t e = cudaMemsetAsync(p->state, 0, sizeof(SearchState), s);
-  if (e == cudaSuccess) e = cudaEventRecordWithFlags(p->ev[0], s, cudaEventRecordExternal);
+  if (e == cudaSuccess) e = record(p->ev[0], s, capturing);
   if (e == cudaSuccess) e = launch_search(p->kc, 0, p->db->view, p->params, p->state, p->scr, s);
-  if (e == cudaSuccess) e = cudaEventRecordWithFlags(p->ev[1], s, cudaEventRecordExternal);
+  if (e == cudaSuccess) e = record(p->ev[1], s, capturing);
   if (e == cudaSuccess) e = launch_search(p->kc, 1, p->db->view, p->params, p->state, p->scr, s);
-  if (e == cudaSuccess) e = cudaEventRecordWithFlags(p->ev[2], s, cudaEventRecordExternal);
+  if (e == cudaSuccess) e = record(p->ev[2], s, capturing);
   return e;
 }
 
 static cudaError_t run_kernels(sw_plan* p, cudaStream_t s) {
-  if (!p->opt.use_graph) return enqueue_kernels(p, s);
+  if (!p->opt.use_graph) return enqueue_kernels(p, s, false);
   if (!p->graph) {
     cudaStream_t cs;
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
@@ -545,7 +552,7 @@ static cudaError_t run_kernels(sw_plan* p, cudaStream_t s) {
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaError_t e2 = enqueue_kernels(p, cs);
+      cudaError_t e2 = enqueue_kernels(p, cs, true);
       e = cudaStreamEndCapture(cs, &g);
       if (e2 != cudaSuccess) e = e2;
     }

@@ -31,7 +31,10 @@ enum IntOp {
   OP_CELL_S16X2 = 10,  // one packed cell-pair update (6 ops, see below)
   OP_CELL_S16X2_PRMT = 11, // the same plus one PRMT (7 ops)
   OP_CELL_I32 = 12,    // Algorithm 1 style int32 cell (10 ops after sharing H-Go)
-  OP_COUNT = 13
+  OP_IMAD = 13,        // int32 multiply-add with a run-time multiplier (FMA pipe)
+  OP_CELL_BIASED = 14, // the packed cell pair of the search kernel: prmt, vimax3,
+                       // viaddmax, imad (H'-Go), viaddmax x2 (6 ops, one on the FMA pipe)
+  OP_COUNT = 15
 };
 
 __host__ __device__ inline int intpeak_ops_per_step(int op) {
@@ -39,6 +42,7 @@ __host__ __device__ inline int intpeak_ops_per_step(int op) {
     case OP_CELL_S16X2: return 6;
     case OP_CELL_S16X2_PRMT: return 7;
     case OP_CELL_I32: return 10;
+    case OP_CELL_BIASED: return 6;
     default: return 1;
   }
 }
@@ -61,6 +65,18 @@ __device__ __forceinline__ void step(uint32_t (&a)[CHAINS], uint32_t c0, uint32_
     else if (OP == OP_VSUB2) r = __vsub2(x, y);
     else if (OP == OP_VADDSS2) r = __vaddss2(x, y);
     else if (OP == OP_PRMT) r = __byte_perm(x, y, 0xC480 + (i & 3) * 0x1111);
+    else if (OP == OP_IMAD) {
+      asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(x), "r"(c1), "r"(y));
+    } else if (OP == OP_CELL_BIASED) {
+      // x: H' diag / F', y: profile source / E'; c0 = Go (both halves), c1 = -Ge
+      uint32_t p, t, one = c0 >> 31 | 1u;
+      asm("prmt.b32 %0, %1, %2, 0xC480;" : "=r"(p) : "r"(y), "r"(x));
+      uint32_t h = __viaddmax_s16x2(x, p, __vimax3_s16x2(y, x, c0));
+      asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(t) : "r"(h), "r"(one), "r"(c1));
+      uint32_t e = __viaddmax_s16x2(y, c1, t);
+      uint32_t f = __viaddmax_s16x2(x, c1, t);
+      r = e ^ f;
+    }
     else if (OP == OP_CELL_S16X2 || OP == OP_CELL_S16X2_PRMT) {
       // x plays H-diag, y the profile word / E, c0 = -Go packed, c1 = -Ge packed
       uint32_t p = y;
@@ -120,6 +136,8 @@ static IntpeakKernel intpeak_pick(int op) {
     case OP_CELL_S16X2: return intpeak_kernel<OP_CELL_S16X2>;
     case OP_CELL_S16X2_PRMT: return intpeak_kernel<OP_CELL_S16X2_PRMT>;
     case OP_CELL_I32: return intpeak_kernel<OP_CELL_I32>;
+    case OP_IMAD: return intpeak_kernel<OP_IMAD>;
+    case OP_CELL_BIASED: return intpeak_kernel<OP_CELL_BIASED>;
     default: return nullptr;
   }
 }
@@ -173,7 +191,7 @@ int intpeak_run(int op, int blocks_per_sm, int threads, int iters, double* lane_
 int main() {
   const char* names[] = {"iadd", "imax", "viaddmax_s32", "viaddmax_s16x2", "viaddmax_s16x2_relu",
                          "vimax3_s16x2", "vmaxs2", "vsub2", "vaddss2", "prmt", "cell_s16x2",
-                         "cell_s16x2_prmt", "cell_i32"};
+                         "cell_s16x2_prmt", "cell_i32", "imad", "cell_biased"};
   for (int op = 0; op < swgb::OP_COUNT; op++) {
     for (int bps : {4, 8}) {
       double r, mhz, s;

@@ -74,9 +74,16 @@ __device__ __forceinline__ uint4 ldg_nc(const uint4* p) {
 // that the 8 lanes of a quarter-warp read 16-byte rows of any residue codes
 // from 8 distinct bank groups (no bank conflicts for random residues):
 //   byte (c, half h, copy p, row r) at ((c * (T/16) + h) * 8 + p) * 16 + (r - 16h)
+// After the profile, the inter-task slice holds two cp.async staging rings:
+// border vectors of the next RING column pairs (one uint4 per lane each) and
+// residue vectors of the next two 8-column chunks (one uint4 per lane each).
+constexpr int RING = 4;
 template <int T>
 struct InterProfile {
-  static constexpr int BYTES = NCODES * 8 * T;
+  static constexpr int PROFILE = NCODES * 8 * T;
+  static constexpr int BORDER_RING = PROFILE;                 // RING x 32 x 16 bytes
+  static constexpr int RES_RING = BORDER_RING + RING * 512;   // 2 x 32 x 16 bytes
+  static constexpr int BYTES = RES_RING + 2 * 512;
 };
 // Intra-task pass profile, int8: lane k's TI rows for code c at (c * 32 + k) * TI.
 template <int TI>
@@ -89,6 +96,19 @@ struct SliceBytes {
   static constexpr int A = InterProfile<T>::BYTES, B = IntraProfile<TI>::BYTES;
   static constexpr int BYTES = ((A > B ? A : B) + 15) / 16 * 16;
 };
+
+// 16-byte asynchronous global -> shared copy (L2 only), and its group fences.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 // ---- score output ------------------------------------------------------------
 __device__ __forceinline__ void emit_score(const DbView& db, const SearchParams* __restrict__ P,
@@ -202,6 +222,50 @@ __device__ void intra_item(const DbView& db, const SearchParams* __restrict__ P,
 }
 
 // ---- inter-task, packed 16-bit pairs (Section II-B, inter-task) ------------
+//
+// Values are held with a bias of +Go: X' = X + Go for H, E, F and S.  Then
+//   * the zero term of Eq. 1 becomes a max with the constant Go, folded into
+//     the three-input max of E' and F';
+//   * every H' is >= Go in each 16-bit half, so t' = H' - Go never borrows
+//     across halves and is one 32-bit integer multiply-add (FMA pipe);
+//   * E' - Ge >= -Ge and H' <= 32767 as long as H <= 32767 - Go: nothing
+//     wraps before a score reaches the recompute threshold.
+// A pair is recomputed in int32 when S' >= 32767 - max(SM): the first cell
+// whose H' could exceed 32767 has exact inputs, so it is recorded in S'.
+__device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t r;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+  return r;
+}
+
+template <int T>
+__device__ __forceinline__ void packed_column(uint32_t (&Hp)[T], uint32_t (&E)[T], uint32_t& hd,
+                                              uint32_t& f, uint32_t& smax, const uint4 (&va)[T / 16],
+                                              const uint4 (&vb)[T / 16], uint32_t GO2, uint32_t NGE2,
+                                              uint32_t MGO, uint32_t one) {
+  uint32_t hprev = 0;
+#pragma unroll
+  for (int r = 0; r < T; r++) {
+    const uint4& A = va[r / 16];
+    const uint4& B = vb[r / 16];
+    const int wq = (r / 4) & 3;
+    const uint32_t a32 = wq == 0 ? A.x : wq == 1 ? A.y : wq == 2 ? A.z : A.w;
+    const uint32_t b32 = wq == 0 ? B.x : wq == 1 ? B.y : wq == 2 ? B.z : B.w;
+    const uint32_t w = prmt(a32, b32, sext_pair_sel(r & 3));  // (SM(q_i, a_j), SM(q_i, b_j))
+    const uint32_t e = E[r];
+    const uint32_t h = __viaddmax_s16x2(hd, w, __vimax3_s16x2(e, f, GO2));  // H'
+    hd = Hp[r];
+    Hp[r] = h;
+    const uint32_t t = imad(h, one, MGO);  // H' - Go in both halves
+    E[r] = __viaddmax_s16x2(e, NGE2, t);   // E' of the next column
+    f = __viaddmax_s16x2(f, NGE2, t);      // F' of the next row
+    if (r & 1)
+      smax = __vimax3_s16x2(smax, hprev, h);
+    else
+      hprev = h;
+  }
+}
+
 template <int T>
 __device__ void inter_item(const DbView& db, const SearchParams* __restrict__ P, SearchState* st,
                            const int8_t* __restrict__ sm, uint8_t* slice, int lane,
@@ -211,11 +275,17 @@ __device__ void inter_item(const DbView& db, const SearchParams* __restrict__ P,
   const uint8_t* __restrict__ qr = P->qres + P->qoff[q];
   const uint4* __restrict__ res = (const uint4*)(db.inter + db.goff[g]) + lane;
   uint4* bd = scr.inter_border + warp_id * scr.inter_stride_vec + lane;
-  const uint32_t GO2 = pack2(P->go), NGE2 = pack2(-P->ge), NGO2 = pack2(-P->go);
+  const int go = P->go;
+  const uint32_t GO2 = pack2(go);                               // H' of H = 0
+  const uint32_t NGE2 = pack2(-P->ge);
+  const uint32_t MGO = (uint32_t)(-(int)((uint32_t)go * 65537u));  // - (Go, Go) as one word
+  const uint32_t ZERO2 = 0u;                                    // E' of E = -Go, F' of F = -Go
+  const uint32_t one = (uint32_t)P->one;
   const int p16 = (lane & 7) * 16;
   constexpr int HALVES = T / 16;
   const int nstrips = L > 0 ? (m + T - 1) / T : 0;
-  uint32_t smax = 0;
+  const int npairs = L / 2;
+  uint32_t smax = GO2;  // S' of S = 0
   for (int s = 0; s < nstrips; s++) {
     __syncwarp();
     if (lane < NCODES) {  // code c = lane: T bytes, written to all 8 copies
@@ -244,82 +314,80 @@ __device__ void inter_item(const DbView& db, const SearchParams* __restrict__ P,
     uint32_t Hp[T], E[T];
 #pragma unroll
     for (int r = 0; r < T; r++) {
-      Hp[r] = 0;     // H(i, 0)
-      E[r] = NGO2;   // E(i, 1)
+      Hp[r] = GO2;    // H(i, 0) = 0
+      E[r] = ZERO2;   // E(i, 1) = -Go
     }
-    uint32_t hdiag = 0;
+    uint32_t hdiag = GO2;
     const bool first = (s == 0), last = (s == nstrips - 1);
-    for (int c = 0; c < L / CHUNK; c++) {
-      const uint4 rr = ldg_nc(res + c * 32);
+    const uint4 INIT = make_uint4(GO2, ZERO2, GO2, ZERO2);  // H(0, j) = 0, F(1, j) = -Go
+    // Staging rings: the border vector of column pair p goes to border slot
+    // p % RING and the residues of chunk c to residue slot c % 2, copied with
+    // cp.async RING - 1 pairs ahead of use (commit group p = pair p).  A slot
+    // is refilled only after the registers read from it were consumed.
+    uint4* bring = (uint4*)(slice + InterProfile<T>::BORDER_RING) + lane;
+    uint4* rring = (uint4*)(slice + InterProfile<T>::RES_RING) + lane;
 #pragma unroll
-      for (int jp = 0; jp < CHUNK / 2; jp++) {
-        // border vector of columns 2jp, 2jp+1: (H, F, H, F) of the row above the strip
-        const uint4 b = first ? make_uint4(0u, NGO2, 0u, NGO2)  // H(0,j) = 0, F(1,j) = -Go
-                              : bd[(c * 4 + jp) * 32];
-        uint4 o;
-#pragma unroll
-        for (int jh = 0; jh < 2; jh++) {
-          const int jj = 2 * jp + jh;
-          const uint32_t wa = jj < 4 ? rr.x : rr.y;
-          const uint32_t wb = jj < 4 ? rr.z : rr.w;
-          const uint32_t ca = (wa >> (8 * (jj & 3))) & 0xffu;
-          const uint32_t cb = (wb >> (8 * (jj & 3))) & 0xffu;
-          uint4 va[HALVES], vb[HALVES];
-#pragma unroll
-          for (int h = 0; h < HALVES; h++) {
-            va[h] = *(const uint4*)(slice + (ca * HALVES + h) * 128 + p16);
-            vb[h] = *(const uint4*)(slice + (cb * HALVES + h) * 128 + p16);
-          }
-          const uint32_t htop = jh ? b.z : b.x;
-          uint32_t f = jh ? b.w : b.y;
-          uint32_t hd = hdiag;
-          hdiag = htop;
-          uint32_t hprev = 0;
-#pragma unroll
-          for (int r = 0; r < T; r++) {
-            const uint4& A = va[r / 16];
-            const uint4& B = vb[r / 16];
-            const int wq = (r / 4) & 3;
-            const uint32_t a32 = wq == 0 ? A.x : wq == 1 ? A.y : wq == 2 ? A.z : A.w;
-            const uint32_t b32 = wq == 0 ? B.x : wq == 1 ? B.y : wq == 2 ? B.z : B.w;
-            const uint32_t w = prmt(a32, b32, sext_pair_sel(r & 3));
-            const uint32_t e = E[r];
-            const uint32_t h = __viaddmax_s16x2_relu(hd, w, __vmaxs2(e, f));
-            hd = Hp[r];
-            Hp[r] = h;
-            const uint32_t t = __vsub2(h, GO2);
-            E[r] = __viaddmax_s16x2(e, NGE2, t);
-            f = __viaddmax_s16x2(f, NGE2, t);
-            if (r & 1)
-              smax = __vimax3_s16x2(smax, hprev, h);
-            else
-              hprev = h;
-          }
-          if (jh) {
-            o.z = Hp[T - 1];
-            o.w = f;
-          } else {
-            o.x = Hp[T - 1];
-            o.y = f;
-          }
-        }
-        if (!last) bd[(c * 4 + jp) * 32] = o;
+    for (int j = 0; j < RING - 1; j++) {
+      if (j < npairs) {
+        if (!first) cp_async16(bring + (j % RING) * 32, bd + j * 32);
+        if ((j & 3) == 0) cp_async16(rring + ((j >> 2) & 1) * 32, res + (j >> 2) * 32);
       }
+      cp_async_commit();
     }
+#pragma unroll 1
+    for (int k = 0; k < npairs; k++) {
+      const int kn = k + RING - 1;
+      if (kn < npairs) {
+        if (!first) cp_async16(bring + (kn % RING) * 32, bd + kn * 32);
+        if ((kn & 3) == 0) cp_async16(rring + ((kn >> 2) & 1) * 32, res + (kn >> 2) * 32);
+      }
+      cp_async_commit();
+      cp_async_wait<RING - 1>();  // pair k's copies have landed
+      const uint4 b = first ? INIT : bring[(k % RING) * 32];
+      const uint4 rr = rring[((k >> 2) & 1) * 32];
+      const uint32_t wa = (k & 2) ? rr.y : rr.x;  // residues of columns 2k, 2k+1
+      const uint32_t wb = (k & 2) ? rr.w : rr.z;
+      const int sh = (k & 1) * 16;
+      uint4 o;
+#pragma unroll
+      for (int jh = 0; jh < 2; jh++) {
+        const uint32_t ca = (wa >> (sh + 8 * jh)) & 0xffu;
+        const uint32_t cb = (wb >> (sh + 8 * jh)) & 0xffu;
+        uint4 va[HALVES], vb[HALVES];
+#pragma unroll
+        for (int h = 0; h < HALVES; h++) {
+          va[h] = *(const uint4*)(slice + (ca * HALVES + h) * 128 + p16);
+          vb[h] = *(const uint4*)(slice + (cb * HALVES + h) * 128 + p16);
+        }
+        uint32_t hd = hdiag;
+        hdiag = jh ? b.z : b.x;           // H of the row above, this column
+        uint32_t f = jh ? b.w : b.y;      // F of the strip's first row, this column
+        packed_column<T>(Hp, E, hd, f, smax, va, vb, GO2, NGE2, MGO, one);
+        if (jh) {
+          o.z = Hp[T - 1];
+          o.w = f;
+        } else {
+          o.x = Hp[T - 1];
+          o.y = f;
+        }
+      }
+      if (!last) bd[k * 32] = o;
+    }
+    cp_async_wait<0>();
   }
-  // two scores per lane; a saturated one goes to the int32 recompute list
+  // two scores per lane; a possibly saturated one goes to the int32 recompute list
   const int base = g * GROUP + 2 * lane;
 #pragma unroll
   for (int half = 0; half < 2; half++) {
     const int sidx = base + half;
     const int orig = db.perm[sidx];
     if (orig < 0) continue;
-    const int score = (int)(int16_t)(half ? (smax >> 16) : (smax & 0xffffu));
-    if (score >= P->sat_threshold) {
+    const int sb = (int)(int16_t)(half ? (smax >> 16) : (smax & 0xffffu));  // S'
+    if (sb >= P->sat_threshold) {
       const unsigned long long k = atomicAdd(&st->n_flags, 1ull);
       if ((int64_t)k < scr.flag_capacity) scr.flags[k] = make_int2(q, sidx);
     } else {
-      P->scores[(int64_t)q * db.n + orig] = score;
+      P->scores[(int64_t)q * db.n + orig] = sb - go;
     }
   }
 }

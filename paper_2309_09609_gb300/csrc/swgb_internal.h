@@ -60,7 +60,8 @@ struct SearchParams {
   int32_t g_first;        // first inter-task group (n_long / GROUP)
   int32_t go;             // Go = gap_open + gap_extend  (Eq. 2-3)
   int32_t ge;             // Ge = gap_extend
-  int32_t sat_threshold;  // a 16-bit score >= this is recomputed in int32
+  int32_t sat_threshold;  // packed path: S + Go >= this (32767 - max SM) is recomputed in int32
+  int32_t one;            // 1, read at run time so multiply-adds stay integer multiply-adds
   int8_t sm[NCODES * NCODES];  // SM(query code, subject code), PAD row/column = PAD_SCORE
 };
 

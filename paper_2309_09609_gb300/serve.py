@@ -1,0 +1,241 @@
+"""Serving loop: a resident database, memory-bounded admission and continuous
+batching over a pool of CUDA-stream slots.
+
+The search itself is the library's (``sw_plan_search_async``); this module
+only schedules it.  A request is one query; its result is the exact score
+row against every subject.
+
+* The database stays resident on the device for the life of the server.
+* Admission: every request needs device memory for its scores row
+  (4 bytes x subjects) and its share of the plan's query/flag buffers; a
+  request is admitted while the bytes of all admitted, unfinished requests
+  stay within ``memory_budget``.  A request that could never fit is refused
+  at once (``AdmissionError``), never queued forever.
+* Continuous batching: a scheduler thread takes the admitted requests that
+  have arrived, up to ``max_batch`` queries and ``max_batch_residues``
+  residues, and launches them as one batch on a free slot (its own plan and
+  CUDA stream).  Requests arriving while earlier batches run go to the next
+  free slot, so batches of different lengths overlap on the GPU.
+* Completion is observed per slot; each request gets its scores, its
+  latency (arrival to completion on the host) and the batch it rode in.
+"""
+from __future__ import annotations
+
+import collections
+import threading
+import time
+from concurrent.futures import Future
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import swgb
+
+
+class AdmissionError(RuntimeError):
+    """The request needs more memory than the server's whole budget."""
+
+
+@dataclass
+class Request:
+    rid: int
+    query: np.ndarray
+    arrival: float
+    future: Future = field(default_factory=Future)
+    admitted: float = 0.0
+    started: float = 0.0
+    finished: float = 0.0
+    batch: int = -1
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+class _Slot:
+    def __init__(self, db, max_batch, max_residues, opts):
+        import torch
+        self.plan = db.plan(max_batch, max_residues, **opts)
+        self.stream = torch.cuda.Stream(device=db.device)
+        self.scores = torch.empty((max_batch, db.n), dtype=torch.int32,
+                                  device=f"cuda:{db.device}")
+        self.requests: list[Request] = []
+        self.batch_id = -1
+
+    @property
+    def busy(self) -> bool:
+        return bool(self.requests)
+
+
+class Server:
+    """Continuous-batching search server over one resident Database."""
+
+    def __init__(self, db: swgb.Database, slots: int = 4, max_batch: int = 16,
+                 max_batch_residues: int = 65536, memory_budget: int | None = None,
+                 gap_open: int = 10, gap_extend: int = 2, matrix=None, **plan_opts):
+        self.db = db
+        self.max_batch = int(max_batch)
+        self.max_batch_residues = int(max_batch_residues)
+        self.gap_open, self.gap_extend, self.matrix = gap_open, gap_extend, matrix
+        self.slots = [_Slot(db, self.max_batch, self.max_batch_residues, plan_opts)
+                      for _ in range(int(slots))]
+        per_row = 4 * db.n
+        self.memory_budget = int(memory_budget) if memory_budget else \
+            len(self.slots) * self.max_batch * per_row * 2
+        self._lock = threading.Condition()
+        self._pending: collections.deque[Request] = collections.deque()
+        self._in_use = 0
+        self._next_id = 0
+        self._batches = 0
+        self.max_concurrent = 0       # most batches in flight at once
+        self._stop = False
+        self.completed: list[Request] = []
+        self._thread = threading.Thread(target=self._loop, daemon=True)
+        self._thread.start()
+
+    # ---- admission ------------------------------------------------------------
+    def request_bytes(self, query_len: int) -> int:
+        """Device bytes a request holds while admitted: its scores row, its
+        residues in the query buffer and its saturation-list share."""
+        return 4 * self.db.n + int(query_len) + 8 * self.db.n
+
+    def submit(self, query, arrival: float | None = None) -> Future:
+        q = np.ascontiguousarray(query, dtype=np.uint8)
+        if q.size and int(q.max()) >= 24:
+            raise ValueError("residue codes must be 0..23")
+        need = self.request_bytes(q.size)
+        if need > self.memory_budget or q.size > self.max_batch_residues:
+            raise AdmissionError(f"request needs {need} bytes / {q.size} residues; budget "
+                                 f"{self.memory_budget} bytes / {self.max_batch_residues} residues")
+        with self._lock:
+            if self._stop:
+                raise RuntimeError("server is closed")
+            r = Request(self._next_id, q, time.perf_counter() if arrival is None else arrival)
+            self._next_id += 1
+            self._pending.append(r)
+            self._lock.notify_all()
+        return r.future
+
+    # ---- scheduler ---------------------------------------------------------------
+    def _take_batch(self):
+        """Admitted requests for one batch (called with the lock held)."""
+        batch, residues = [], 0
+        while self._pending and len(batch) < self.max_batch:
+            r = self._pending[0]
+            need = self.request_bytes(r.query.size)
+            if residues + r.query.size > self.max_batch_residues:
+                break
+            if self._in_use + need > self.memory_budget:
+                break
+            self._pending.popleft()
+            self._in_use += need
+            r.admitted = time.perf_counter()
+            batch.append(r)
+            residues += r.query.size
+        return batch
+
+    def _launch(self, slot: _Slot, batch: list[Request]):
+        q = np.concatenate([r.query for r in batch]) if batch else np.zeros(0, np.uint8)
+        lens = np.array([r.query.size for r in batch], dtype=np.int32)
+        out = slot.scores[:len(batch)]
+        now = time.perf_counter()
+        for r in batch:
+            r.started = now
+            r.batch = self._batches
+        slot.batch_id = self._batches
+        self._batches += 1
+        slot.requests = batch
+        slot.plan.search_async(q, lens, out, self.gap_open, self.gap_extend, self.matrix,
+                               stream=slot.stream)
+        self.max_concurrent = max(self.max_concurrent, sum(s.busy for s in self.slots))
+
+    def _complete(self, slot: _Slot):
+        batch = slot.requests
+        rows = slot.scores[:len(batch)].cpu().numpy()  # the slot's stream has finished
+        now = time.perf_counter()
+        with self._lock:
+            for i, r in enumerate(batch):
+                r.finished = now
+                self._in_use -= self.request_bytes(r.query.size)
+                self.completed.append(r)
+            slot.requests = []
+            self._lock.notify_all()
+        for i, r in enumerate(batch):
+            r.future.set_result(rows[i].copy())
+
+    def _loop(self):
+        import torch
+        torch.cuda.set_device(self.db.device)
+        while True:
+            progressed = False
+            for s in self.slots:
+                if s.busy:
+                    try:
+                        done = s.plan.wait(0)
+                    except Exception as e:  # a failed batch fails its requests only
+                        for r in s.requests:
+                            r.future.set_exception(e)
+                        with self._lock:
+                            for r in s.requests:
+                                self._in_use -= self.request_bytes(r.query.size)
+                            s.requests = []
+                        progressed = True
+                        continue
+                    if done:
+                        self._complete(s)
+                        progressed = True
+            with self._lock:
+                if self._stop and not self._pending and not any(s.busy for s in self.slots):
+                    return
+                free = [s for s in self.slots if not s.busy]
+                batch = self._take_batch() if free and self._pending else []
+            if batch:
+                try:
+                    self._launch(free[0], batch)
+                except Exception as e:
+                    with self._lock:
+                        for r in batch:
+                            self._in_use -= self.request_bytes(r.query.size)
+                    free[0].requests = []
+                    for r in batch:
+                        r.future.set_exception(e)
+                progressed = True
+            if not progressed:
+                with self._lock:
+                    self._lock.wait(0.0002)
+
+    def close(self, timeout: float = 600.0):
+        with self._lock:
+            self._stop = True
+            self._lock.notify_all()
+        self._thread.join(timeout)
+        for s in self.slots:
+            s.plan.close()
+
+    # ---- reporting --------------------------------------------------------------
+    def report(self, wall_s: float | None = None) -> dict:
+        lat = np.array([r.latency for r in self.completed]) * 1e3
+        cells = sum(r.query.size for r in self.completed) * self.db.residues
+        if wall_s is None and self.completed:
+            wall_s = max(r.finished for r in self.completed) - min(r.arrival for r in self.completed)
+        return {"requests": len(self.completed), "batches": self._batches,
+                "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
+                "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
+                "mean_batch": len(self.completed) / max(self._batches, 1),
+                "max_concurrent_batches": self.max_concurrent,
+                "gcups": cells / wall_s / 1e9 if wall_s else None, "wall_s": wall_s}
+
+
+def replay(server: Server, arrivals, speed: float = 1.0, timeout: float = 600.0):
+    """Submits a trace (synth.Arrivals) at its arrival times; returns futures."""
+    t0 = time.perf_counter()
+    futs = []
+    for i in range(len(arrivals.queries)):
+        target = t0 + arrivals.times[i] / speed
+        delay = target - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        futs.append(server.submit(arrivals.queries.seq(i), arrival=max(target, t0)))
+    for f in futs:
+        f.result(timeout)
+    return futs

@@ -1,0 +1,49 @@
+"""The N > 1 host path of bench.py on CPU: two gloo ranks, barrier and the
+max-over-ranks timing reduction (each rank runs an independent replica; the
+search itself has no collective)."""
+import os
+import socket
+import subprocess
+import sys
+import textwrap
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+CHILD = textwrap.dedent("""
+    import os, sys
+    sys.path.insert(0, {root!r})
+    os.environ["SWGB_BENCH_BACKEND"] = "gloo"
+    import bench
+    rank, world, local, dist = bench.dist_setup(None)
+    assert world == 2 and dist is not None
+    dist.barrier()
+    t = bench.max_over_ranks(10.0 + rank, dist, "cpu")
+    assert t == 11.0, t
+    dist.barrier()
+    dist.destroy_process_group()
+    print("ok", rank)
+""")
+
+
+def test_two_gloo_ranks_reduce_max_time():
+    port = _free_port()
+    procs = []
+    for rank in range(2):
+        env = dict(os.environ, RANK=str(rank), LOCAL_RANK=str(rank), WORLD_SIZE="2",
+                   MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+        procs.append(subprocess.Popen([sys.executable, "-c", CHILD.format(root=ROOT)], env=env,
+                                      stdout=subprocess.PIPE, stderr=subprocess.STDOUT,
+                                      text=True))
+    outs = [p.communicate(timeout=120)[0] for p in procs]
+    for rank, (p, out) in enumerate(zip(procs, outs)):
+        assert p.returncode == 0, out
+        assert f"ok {rank}" in out
