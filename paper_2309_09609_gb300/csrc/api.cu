@@ -367,6 +367,9 @@ static sw_status fill_scoring(SearchParams& P, int32_t gap_open, int32_t gap_ext
   P.ge = gap_extend;
   P.sat_threshold = S16_LIMIT - maxsm;
   P.one = 1;
+  // biased 16-bit border above row 1: H' = 0 + Go, F' = -Go + Go (both subjects)
+  const uint32_t go2 = ((uint32_t)(uint16_t)P.go) * 0x00010001u;
+  P.init_border = make_uint4(go2, 0u, go2, 0u);
   *packed_ok = (P.go + P.ge) <= kPackedMaxGap;
   return SW_OK;
 }

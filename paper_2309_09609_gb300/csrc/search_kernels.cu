@@ -74,16 +74,16 @@ __device__ __forceinline__ uint4 ldg_nc(const uint4* p) {
 // that the 8 lanes of a quarter-warp read 16-byte rows of any residue codes
 // from 8 distinct bank groups (no bank conflicts for random residues):
 //   byte (c, half h, copy p, row r) at ((c * (T/16) + h) * 8 + p) * 16 + (r - 16h)
-// After the profile, the inter-task slice holds two cp.async staging rings:
-// border vectors of the next RING column pairs (one uint4 per lane each) and
-// residue vectors of the next two 8-column chunks (one uint4 per lane each).
-constexpr int RING = 4;
+// After the profile, the inter-task slice holds the cp.async staging ring of
+// CRING 8-column chunks: per chunk, the 4 border vectors (one per column pair)
+// and the residue vector of every lane.
+constexpr int CRING = 3;  // chunks in flight per warp
 template <int T>
 struct InterProfile {
   static constexpr int PROFILE = NCODES * 8 * T;
-  static constexpr int BORDER_RING = PROFILE;                 // RING x 32 x 16 bytes
-  static constexpr int RES_RING = BORDER_RING + RING * 512;   // 2 x 32 x 16 bytes
-  static constexpr int BYTES = RES_RING + 2 * 512;
+  static constexpr int BORDER_RING = PROFILE;                     // CRING x 4 x 32 x 16 bytes
+  static constexpr int RES_RING = BORDER_RING + CRING * 4 * 512;  // CRING x 32 x 16 bytes
+  static constexpr int BYTES = RES_RING + CRING * 512;
 };
 // Intra-task pass profile, int8: lane k's TI rows for code c at (c * 32 + k) * TI.
 template <int TI>
@@ -267,6 +267,37 @@ __device__ __forceinline__ void packed_column(uint32_t (&Hp)[T], uint32_t (&E)[T
 }
 
 template <int T>
+__device__ __forceinline__ void packed_pair(uint32_t (&Hp)[T], uint32_t (&E)[T], uint32_t& hdiag,
+                                            uint32_t& smax, const uint8_t* slice, int p16,
+                                            uint32_t wa, uint32_t wb, const uint4& b, uint4& o,
+                                            int byte0, uint32_t GO2, uint32_t NGE2, uint32_t MGO,
+                                            uint32_t one) {
+  constexpr int HALVES = T / 16;
+#pragma unroll
+  for (int jh = 0; jh < 2; jh++) {
+    const uint32_t ca = (wa >> (8 * (byte0 + jh))) & 0xffu;
+    const uint32_t cb = (wb >> (8 * (byte0 + jh))) & 0xffu;
+    uint4 va[HALVES], vb[HALVES];
+#pragma unroll
+    for (int h = 0; h < HALVES; h++) {
+      va[h] = *(const uint4*)(slice + (ca * HALVES + h) * 128 + p16);
+      vb[h] = *(const uint4*)(slice + (cb * HALVES + h) * 128 + p16);
+    }
+    uint32_t hd = hdiag;
+    hdiag = jh ? b.z : b.x;       // H of the row above the strip, this column
+    uint32_t f = jh ? b.w : b.y;  // F of the strip's first row, this column
+    packed_column<T>(Hp, E, hd, f, smax, va, vb, GO2, NGE2, MGO, one);
+    if (jh) {
+      o.z = Hp[T - 1];
+      o.w = f;
+    } else {
+      o.x = Hp[T - 1];
+      o.y = f;
+    }
+  }
+}
+
+template <int T>
 __device__ void inter_item(const DbView& db, const SearchParams* __restrict__ P, SearchState* st,
                            const int8_t* __restrict__ sm, uint8_t* slice, int lane,
                            int64_t warp_id, const Scratch& scr, int q, int g) {
@@ -276,15 +307,17 @@ __device__ void inter_item(const DbView& db, const SearchParams* __restrict__ P,
   const uint4* __restrict__ res = (const uint4*)(db.inter + db.goff[g]) + lane;
   uint4* bd = scr.inter_border + warp_id * scr.inter_stride_vec + lane;
   const int go = P->go;
-  const uint32_t GO2 = pack2(go);                               // H' of H = 0
+  const uint32_t GO2 = pack2(go);                                  // H' of H = 0
   const uint32_t NGE2 = pack2(-P->ge);
   const uint32_t MGO = (uint32_t)(-(int)((uint32_t)go * 65537u));  // - (Go, Go) as one word
-  const uint32_t ZERO2 = 0u;                                    // E' of E = -Go, F' of F = -Go
+  const uint32_t ZERO2 = 0u;                                       // E' of E = -Go
   const uint32_t one = (uint32_t)P->one;
   const int p16 = (lane & 7) * 16;
   constexpr int HALVES = T / 16;
   const int nstrips = L > 0 ? (m + T - 1) / T : 0;
-  const int npairs = L / 2;
+  const int nch = L / CHUNK;
+  uint4* bring = (uint4*)(slice + InterProfile<T>::BORDER_RING) + lane;  // [slot][pair][lane]
+  uint4* rring = (uint4*)(slice + InterProfile<T>::RES_RING) + lane;     // [slot][lane]
   uint32_t smax = GO2;  // S' of S = 0
   for (int s = 0; s < nstrips; s++) {
     __syncwarp();
@@ -318,60 +351,52 @@ __device__ void inter_item(const DbView& db, const SearchParams* __restrict__ P,
       E[r] = ZERO2;   // E(i, 1) = -Go
     }
     uint32_t hdiag = GO2;
-    const bool first = (s == 0), last = (s == nstrips - 1);
-    const uint4 INIT = make_uint4(GO2, ZERO2, GO2, ZERO2);  // H(0, j) = 0, F(1, j) = -Go
-    // Staging rings: the border vector of column pair p goes to border slot
-    // p % RING and the residues of chunk c to residue slot c % 2, copied with
-    // cp.async RING - 1 pairs ahead of use (commit group p = pair p).  A slot
-    // is refilled only after the registers read from it were consumed.
-    uint4* bring = (uint4*)(slice + InterProfile<T>::BORDER_RING) + lane;
-    uint4* rring = (uint4*)(slice + InterProfile<T>::RES_RING) + lane;
+    const bool last = (s == nstrips - 1);
+    // Staging ring of CRING chunks, copied with cp.async CRING - 1 chunks ahead
+    // (commit group c = chunk c).  The first strip's border is the row above
+    // the matrix, (H, F) = (0, -Go) for every column: it is copied from the
+    // parameter block, so the compute loop has no branch on it.  A slot is
+    // refilled only after the registers read from it were consumed.
+    const uint4* bsrc = s == 0 ? (const uint4*)&P->init_border : bd;
+    const int bstep = s == 0 ? 0 : 32;
 #pragma unroll
-    for (int j = 0; j < RING - 1; j++) {
-      if (j < npairs) {
-        if (!first) cp_async16(bring + (j % RING) * 32, bd + j * 32);
-        if ((j & 3) == 0) cp_async16(rring + ((j >> 2) & 1) * 32, res + (j >> 2) * 32);
+    for (int j = 0; j < CRING - 1; j++) {
+      if (j < nch) {
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+          cp_async16(bring + ((j % CRING) * 4 + k) * 32, bsrc + (j * 4 + k) * bstep);
+        cp_async16(rring + (j % CRING) * 32, res + j * 32);
       }
       cp_async_commit();
     }
 #pragma unroll 1
-    for (int k = 0; k < npairs; k++) {
-      const int kn = k + RING - 1;
-      if (kn < npairs) {
-        if (!first) cp_async16(bring + (kn % RING) * 32, bd + kn * 32);
-        if ((kn & 3) == 0) cp_async16(rring + ((kn >> 2) & 1) * 32, res + (kn >> 2) * 32);
+    for (int c = 0; c < nch; c++) {
+      const int cn = c + CRING - 1;
+      if (cn < nch) {
+        const int sl = cn % CRING;
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+          cp_async16(bring + (sl * 4 + k) * 32, bsrc + (cn * 4 + k) * bstep);
+        cp_async16(rring + sl * 32, res + cn * 32);
       }
       cp_async_commit();
-      cp_async_wait<RING - 1>();  // pair k's copies have landed
-      const uint4 b = first ? INIT : bring[(k % RING) * 32];
-      const uint4 rr = rring[((k >> 2) & 1) * 32];
-      const uint32_t wa = (k & 2) ? rr.y : rr.x;  // residues of columns 2k, 2k+1
-      const uint32_t wb = (k & 2) ? rr.w : rr.z;
-      const int sh = (k & 1) * 16;
-      uint4 o;
+      cp_async_wait<CRING - 1>();  // chunk c has landed
+      const int slot = c % CRING;
+      const uint4 rr = rring[slot * 32];
+#pragma unroll 1
+      for (int hq = 0; hq < 2; hq++) {  // 4 columns: one residue word per subject
+        const uint32_t wa = hq ? rr.y : rr.x;
+        const uint32_t wb = hq ? rr.w : rr.z;
 #pragma unroll
-      for (int jh = 0; jh < 2; jh++) {
-        const uint32_t ca = (wa >> (sh + 8 * jh)) & 0xffu;
-        const uint32_t cb = (wb >> (sh + 8 * jh)) & 0xffu;
-        uint4 va[HALVES], vb[HALVES];
-#pragma unroll
-        for (int h = 0; h < HALVES; h++) {
-          va[h] = *(const uint4*)(slice + (ca * HALVES + h) * 128 + p16);
-          vb[h] = *(const uint4*)(slice + (cb * HALVES + h) * 128 + p16);
-        }
-        uint32_t hd = hdiag;
-        hdiag = jh ? b.z : b.x;           // H of the row above, this column
-        uint32_t f = jh ? b.w : b.y;      // F of the strip's first row, this column
-        packed_column<T>(Hp, E, hd, f, smax, va, vb, GO2, NGE2, MGO, one);
-        if (jh) {
-          o.z = Hp[T - 1];
-          o.w = f;
-        } else {
-          o.x = Hp[T - 1];
-          o.y = f;
+        for (int jp = 0; jp < 2; jp++) {
+          const int pair = hq * 2 + jp;
+          const uint4 b = bring[(slot * 4 + pair) * 32];
+          uint4 o;
+          packed_pair<T>(Hp, E, hdiag, smax, slice, p16, wa, wb, b, o, 2 * jp, GO2, NGE2, MGO,
+                         one);
+          if (!last) bd[(c * 4 + pair) * 32] = o;
         }
       }
-      if (!last) bd[k * 32] = o;
     }
     cp_async_wait<0>();
   }

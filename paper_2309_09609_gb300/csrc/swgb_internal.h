@@ -48,6 +48,7 @@ struct DbView {
 // Kept in device memory (not kernel arguments) so that one captured CUDA graph
 // serves every batch: a new search only rewrites this block.
 struct SearchParams {
+  uint4 init_border;      // packed (H', F') of the row above the matrix: (Go, 0, Go, 0)
   const uint8_t* qres;    // concatenated query codes
   const int64_t* qoff;    // [nq]
   const int32_t* qlen;    // [nq]
