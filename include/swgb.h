@@ -170,6 +170,40 @@ sw_status sw_search_plain(sw_db* db, const uint8_t* queries, const int32_t* q_le
                           int32_t n_queries, int32_t gap_open, int32_t gap_extend,
                           const int8_t* matrix, int32_t* scores, void* stream);
 
+/* Exact scores of every (query, subject) pair without allocating any memory.
+ * The paper has no counterpart: this entry point serves callers that cannot
+ * let a library allocate -- a host framework that owns all device memory
+ * through its own pool, or a service that must not allocate once it is
+ * serving, so that its memory use stays fixed and no call can fail for lack
+ * of memory.  Every other search entry point allocates (a database, a plan,
+ * kernel scratch); this one calls no cudaMalloc, cudaFree or other allocating
+ * routine.
+ *   queries, subjects:     concatenated residue codes, device memory.
+ *   q_offsets, s_offsets:  int64 start of each sequence, device memory.
+ *   q_lengths, s_lengths:  int32 lengths, device memory; subjects may be at
+ *                          most 4096 residues long, queries any length.
+ *   matrix:                24 x 24 int8 SM(query, subject), HOST memory
+ *                          (NULL = BLOSUM62).
+ *   scores:                n_queries x n_subjects int32, device memory.
+ * Same gap convention and the same scores as sw_search.  The kernel's
+ * scratch (one border row per warp, a work counter, a status word) is a
+ * file-scope device array of ~16 MiB that every GPU loading the library holds
+ * until the process exits; the counter and status are cleared at the start of
+ * every call.  The first call on a device looks the array's address up on
+ * that device (the device must be current); make that first call before any
+ * stream capture.  All calls share the one array, so calls whose work
+ * overlaps on the GPU (other streams, other threads) race: serialize them.
+ * The call returns after the scores are written (it synchronizes the stream).
+ * Errors: SW_EINVAL for negative counts or gaps, a NULL buffer, a negative
+ * length, a subject longer than 4096 residues or a code >= 24 (such pairs are
+ * not scored); SW_ECUDA. */
+sw_status sw_search_pairs_noalloc(const uint8_t* queries, const int64_t* q_offsets,
+                                  const int32_t* q_lengths, int32_t n_queries,
+                                  const uint8_t* subjects, const int64_t* s_offsets,
+                                  const int32_t* s_lengths, int32_t n_subjects,
+                                  int32_t gap_open, int32_t gap_extend, const int8_t* matrix,
+                                  int32_t* scores, void* stream);
+
 /* Integer-pipe microbenchmark (Section III-B, Eq. 4: the throughput term,
  * measured instead of looked up).  op selects an instruction kind (0 iadd,
  * 1 imax, 2 viaddmax_s32, 3 viaddmax_s16x2, 4 viaddmax_s16x2_relu,

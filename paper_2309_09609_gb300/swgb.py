@@ -82,6 +82,7 @@ def lib():
             "sw_search": (i32, [P, P, P, i32, i32, i32, P, P, P]),
             "sw_search_plain": (i32, [P, P, P, i32, i32, i32, P, P, P]),
             "sw_intpeak": (i32, [i32, i32, i32, i32, P]),
+            "sw_search_pairs_noalloc": (i32, [P, P, P, i32, P, P, P, i32, i32, i32, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -299,6 +300,19 @@ class Plan:
         s = Stats()
         _check(lib().sw_plan_stats(self._h, ctypes.byref(s)))
         return s.as_dict()
+
+
+def search_pairs_noalloc(queries, q_offsets, q_lengths, subjects, s_offsets, s_lengths, scores,
+                         gap_open=10, gap_extend=2, matrix=None, stream=None):
+    """sw_search_pairs_noalloc: all pairs, for callers that cannot let the
+    library allocate.  Every array is caller-owned CUDA memory (torch CUDA
+    tensors) except `matrix` (host); subjects are at most 4096 residues."""
+    m = _matrix(matrix)
+    _check(lib().sw_search_pairs_noalloc(
+        _ptr(queries), _ptr(q_offsets), _ptr(q_lengths), int(q_lengths.shape[0]),
+        _ptr(subjects), _ptr(s_offsets), _ptr(s_lengths), int(s_lengths.shape[0]),
+        gap_open, gap_extend, _ptr(m), _ptr(scores), _stream(stream)))
+    return scores
 
 
 def intpeak(op, blocks_per_sm: int = 8, threads: int = 256, iters: int = 20000):
