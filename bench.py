@@ -58,7 +58,8 @@ def parse():
                     help="fraction of subjects the CPU oracle baseline searches")
     ap.add_argument("--subjects", type=int, default=None,
                     help="shrink the database (profiling / small cases)")
-    ap.add_argument("--queries", type=int, default=None, help="keep only the first N queries")
+    ap.add_argument("--queries", type=int, default=None, help="keep only N queries")
+    ap.add_argument("--query-offset", type=int, default=0, help="first query kept by --queries")
     ap.add_argument("--serve", type=int, default=200,
                     help="serving leg: arrivals replayed against the resident DB (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=50.0, help="Poisson arrival rate (1/s)")
@@ -69,16 +70,16 @@ def parse():
     return ap.parse_args()
 
 
-def make_workload(name, seed, subjects=None, queries=None):
+def make_workload(name, seed, subjects=None, queries=None, query_offset=0):
     from paper_2309_09609_gb300 import synth
     kw = {}
     if subjects and name in ("paper-search", "batched-uneven", "long"):
         kw["n_subjects"] = subjects
     w = {"paper-search": synth.paper_search, "plain-small": synth.plain_small,
          "batched-uneven": synth.batched_uneven, "long": synth.long_sequences}[name](seed, **kw)
-    if queries and queries < len(w.queries):
-        w.queries = w.queries.subset(range(queries))
-        w.name += f" (first {queries} queries)"
+    if queries and queries + query_offset <= len(w.queries) and queries < len(w.queries):
+        w.queries = w.queries.subset(range(query_offset, query_offset + queries))
+        w.name += f" (queries {query_offset}..{query_offset + queries - 1})"
     return w
 
 
@@ -185,7 +186,7 @@ def run_reference(args):
         return
     import oracle
     oracle.build()
-    w = make_workload(args.workload, args.seed, args.subjects, args.queries)
+    w = make_workload(args.workload, args.seed, args.subjects, args.queries, args.query_offset)
     frac = min(args.cpu_sample, 0.002) if args.workload == "paper-search" else args.cpu_sample
     sub = oracle_sample(w, frac)
     cores = os.cpu_count() or 1
@@ -246,7 +247,7 @@ def run_native(args):
     __graft_entry__.build()
     from paper_2309_09609_gb300 import swgb
 
-    w = make_workload(args.workload, args.seed, args.subjects, args.queries)
+    w = make_workload(args.workload, args.seed, args.subjects, args.queries, args.query_offset)
     q, db = w.queries, w.db
     nq, N = len(q), len(db)
     cells = w.cells

@@ -97,6 +97,10 @@ typedef struct {
   int32_t intra_rows;        /* query rows per lane in the intra-task kernel: 8 or 16 */
   int32_t use_graph;         /* 1: capture the launch sequence in a CUDA graph */
   int32_t force_int32;       /* 1: all subjects through the int32 intra-task kernel */
+  int32_t auto_cutoff;       /* 1: per search of >= 1e10 cells, also send to the intra-task
+                                kernel every group whose (query, group) work item would
+                                exceed a quarter of one warp's share of the search (load
+                                balance for few long queries); default 0 */
 } sw_options;
 
 void sw_options_default(sw_options* opt);

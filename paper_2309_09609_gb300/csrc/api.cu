@@ -99,12 +99,13 @@ extern "C" void sw_default_matrix(int8_t* out) {
 
 extern "C" void sw_options_default(sw_options* opt) {
   if (!opt) return;
-  opt->rows_per_thread = 16;
+  opt->rows_per_thread = 32;
   opt->warps_per_block = 8;
   opt->long_cutoff = 7000;
   opt->intra_rows = 8;
   opt->use_graph = 1;
   opt->force_int32 = 0;
+  opt->auto_cutoff = 0;
 }
 
 // ---- small helpers ----------------------------------------------------------------
@@ -342,6 +343,8 @@ static sw_status read_batch(const uint8_t* queries, const int32_t* q_lengths, in
 // Largest gap penalty sum kept on the packed 16-bit path: E and F stay
 // >= -(Go + Ge) >= -32768 there.
 static constexpr int kPackedMaxGap = 16384;
+// Searches smaller than this many cells skip the load-balancing cutoff.
+static constexpr double kAutoCutoffMinCells = 1e10;
 static constexpr int kMaxGap = 100000000;
 
 static sw_status fill_scoring(SearchParams& P, int32_t gap_open, int32_t gap_extend,
@@ -583,7 +586,19 @@ static sw_status plan_enqueue(sw_plan* p, const HostBatch& hb, int32_t nq, int32
   sw_status st = fill_scoring(P, gap_open, gap_extend, matrix, &packed_ok);
   if (st != SW_OK) return st;
   const DbView& v = p->db->view;
-  const int32_t gf = packed_ok ? p->g_first : v.groups;
+  int32_t gf = packed_ok ? p->g_first : v.groups;
+  const double total_cells = (double)hb.total * (double)p->db->residues;
+  if (packed_ok && p->opt.auto_cutoff && total_cells >= kAutoCutoffMinCells) {
+    // Load balance: a (query, group) item is 64 subjects x the group length x
+    // the query length.  Groups whose largest item exceeds a quarter of one
+    // warp's share of the search go to the intra-task kernel instead, where
+    // each subject is its own item.  Groups are sorted longest first.  Small
+    // searches (a few milliseconds) are left alone.
+    const double warps = (double)p->kc.blocks * p->kc.warps;
+    const double share = total_cells / warps;
+    const int32_t mmax = hb.len[hb.order[0]];
+    while (gf < v.groups && (double)GROUP * p->db->glen_h[gf] * mmax > 0.25 * share) gf++;
+  }
   const int64_t n_long = std::min<int64_t>(v.n, (int64_t)gf * GROUP);
   P.qres = p->qres;
   P.qoff = p->qoff;

@@ -238,63 +238,95 @@ __device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) {
   return r;
 }
 
+// Profile word of row r for this lane's two subjects: (SM(q_r, a_j), SM(q_r, b_j)).
 template <int T>
-__device__ __forceinline__ void packed_column(uint32_t (&Hp)[T], uint32_t (&E)[T], uint32_t& hd,
-                                              uint32_t& f, uint32_t& smax, const uint4 (&va)[T / 16],
-                                              const uint4 (&vb)[T / 16], uint32_t GO2, uint32_t NGE2,
-                                              uint32_t MGO, uint32_t one) {
-  uint32_t hprev = 0;
-#pragma unroll
-  for (int r = 0; r < T; r++) {
-    const uint4& A = va[r / 16];
-    const uint4& B = vb[r / 16];
-    const int wq = (r / 4) & 3;
-    const uint32_t a32 = wq == 0 ? A.x : wq == 1 ? A.y : wq == 2 ? A.z : A.w;
-    const uint32_t b32 = wq == 0 ? B.x : wq == 1 ? B.y : wq == 2 ? B.z : B.w;
-    const uint32_t w = prmt(a32, b32, sext_pair_sel(r & 3));  // (SM(q_i, a_j), SM(q_i, b_j))
-    const uint32_t e = E[r];
-    const uint32_t h = __viaddmax_s16x2(hd, w, __vimax3_s16x2(e, f, GO2));  // H'
-    hd = Hp[r];
-    Hp[r] = h;
-    const uint32_t t = imad(h, one, MGO);  // H' - Go in both halves
-    E[r] = __viaddmax_s16x2(e, NGE2, t);   // E' of the next column
-    f = __viaddmax_s16x2(f, NGE2, t);      // F' of the next row
-    if (r & 1)
-      smax = __vimax3_s16x2(smax, hprev, h);
-    else
-      hprev = h;
-  }
+__device__ __forceinline__ uint32_t profile_word(const uint4 (&va)[T / 16], const uint4 (&vb)[T / 16],
+                                                 int r) {
+  const uint4& A = va[r / 16];
+  const uint4& B = vb[r / 16];
+  const int wq = (r / 4) & 3;
+  const uint32_t a32 = wq == 0 ? A.x : wq == 1 ? A.y : wq == 2 ? A.z : A.w;
+  const uint32_t b32 = wq == 0 ? B.x : wq == 1 ? B.y : wq == 2 ? B.z : B.w;
+  return prmt(a32, b32, sext_pair_sel(r & 3));
 }
 
+// One packed cell update (Eq. 1-3, biased by +Go): returns H'; updates E' of
+// the next column in e and F' of the next row in f.
+__device__ __forceinline__ uint32_t packed_cell(uint32_t hd, uint32_t w, uint32_t& e, uint32_t& f,
+                                                uint32_t GO2, uint32_t NGE2, uint32_t MGO,
+                                                uint32_t one) {
+  const uint32_t h = __viaddmax_s16x2(hd, w, __vimax3_s16x2(e, f, GO2));  // H'
+  const uint32_t t = imad(h, one, MGO);  // H' - Go in both halves (FMA pipe)
+  e = __viaddmax_s16x2(e, NGE2, t);      // E' of the next column
+  f = __viaddmax_s16x2(f, NGE2, t);      // F' of the next row
+  return h;
+}
+
+// Four adjacent columns of T rows as a wavefront: at step k, column c
+// updates row k - c.  Column c's row r needs E' of column c - 1 at row r
+// (written one step earlier) and its H' at row r - 1 (two steps earlier), so
+// the up to four updates of a step are independent.  Hp[r] / E[r] hold H' / E'
+// of the previous column on entry and of the fourth column on exit; b0, b1
+// are the border vectors (H'_c, F'_c) above the strip for columns 0,1 and 2,3;
+// o0, o1 receive the strip's bottom row in the same layout.
 template <int T>
-__device__ __forceinline__ void packed_pair(uint32_t (&Hp)[T], uint32_t (&E)[T], uint32_t& hdiag,
+__device__ __forceinline__ void packed_quad(uint32_t (&Hp)[T], uint32_t (&E)[T], uint32_t& hdiag,
                                             uint32_t& smax, const uint8_t* slice, int p16,
-                                            uint32_t wa, uint32_t wb, const uint4& b, uint4& o,
-                                            int byte0, uint32_t GO2, uint32_t NGE2, uint32_t MGO,
-                                            uint32_t one) {
+                                            uint32_t wa, uint32_t wb, const uint4& b0,
+                                            const uint4& b1, uint4& o0, uint4& o1, uint32_t GO2,
+                                            uint32_t NGE2, uint32_t MGO, uint32_t one) {
   constexpr int HALVES = T / 16;
+  constexpr int W = 4;
+  uint4 pa[W][HALVES], pb[W][HALVES];
 #pragma unroll
-  for (int jh = 0; jh < 2; jh++) {
-    const uint32_t ca = (wa >> (8 * (byte0 + jh))) & 0xffu;
-    const uint32_t cb = (wb >> (8 * (byte0 + jh))) & 0xffu;
-    uint4 va[HALVES], vb[HALVES];
+  for (int c = 0; c < W; c++) {
+    const uint32_t ca = (wa >> (8 * c)) & 0xffu;
+    const uint32_t cb = (wb >> (8 * c)) & 0xffu;
 #pragma unroll
     for (int h = 0; h < HALVES; h++) {
-      va[h] = *(const uint4*)(slice + (ca * HALVES + h) * 128 + p16);
-      vb[h] = *(const uint4*)(slice + (cb * HALVES + h) * 128 + p16);
-    }
-    uint32_t hd = hdiag;
-    hdiag = jh ? b.z : b.x;       // H of the row above the strip, this column
-    uint32_t f = jh ? b.w : b.y;  // F of the strip's first row, this column
-    packed_column<T>(Hp, E, hd, f, smax, va, vb, GO2, NGE2, MGO, one);
-    if (jh) {
-      o.z = Hp[T - 1];
-      o.w = f;
-    } else {
-      o.x = Hp[T - 1];
-      o.y = f;
+      pa[c][h] = *(const uint4*)(slice + (ca * HALVES + h) * 128 + p16);
+      pb[c][h] = *(const uint4*)(slice + (cb * HALVES + h) * 128 + p16);
     }
   }
+  const uint32_t htop[W] = {b0.x, b0.z, b1.x, b1.z};  // H' above the strip, per column
+  uint32_t f[W] = {b0.y, b0.w, b1.y, b1.w};           // F' of the strip's first row
+  uint32_t last[W] = {0, 0, 0, 0}, last2[W] = {0, 0, 0, 0}, bottom[W] = {0, 0, 0, 0};
+  uint32_t hd0 = hdiag;  // column 0's diagonal: previous column, previous row
+  hdiag = htop[W - 1];
+#pragma unroll
+  for (int k = 0; k < T + W - 1; k++) {
+    uint32_t out[W] = {0, 0, 0, 0};
+#pragma unroll
+    for (int c = 0; c < W; c++) {
+      const int r = k - c;
+      if (r < 0 || r >= T) continue;
+      uint32_t hd;
+      if (c == 0) {
+        hd = hd0;
+        hd0 = Hp[r];
+      } else {
+        hd = r == 0 ? htop[c - 1] : last2[c - 1];  // H' of column c - 1, row r - 1
+      }
+      uint32_t e = E[r];
+      out[c] = packed_cell(hd, profile_word<T>(pa[c], pb[c], r), e, f[c], GO2, NGE2, MGO, one);
+      E[r] = e;
+      if (c == W - 1) Hp[r] = out[c];
+      if (r == T - 1) bottom[c] = out[c];
+    }
+    // S' over this step's cells (pairs through a three-input max)
+    const int lo = k - (T - 1) > 0 ? k - (T - 1) : 0;
+    const int hi = k < W - 1 ? k : W - 1;
+    int c = lo;
+    for (; c + 1 <= hi; c += 2) smax = __vimax3_s16x2(smax, out[c], out[c + 1]);
+    if (c == hi) smax = __vmaxs2(smax, out[c]);
+#pragma unroll
+    for (int c2 = 0; c2 < W; c2++) {
+      last2[c2] = last[c2];
+      last[c2] = out[c2];
+    }
+  }
+  o0 = make_uint4(bottom[0], f[0], bottom[1], f[1]);
+  o1 = make_uint4(bottom[2], f[2], bottom[3], f[3]);
 }
 
 template <int T>
@@ -383,19 +415,28 @@ __device__ void inter_item(const DbView& db, const SearchParams* __restrict__ P,
       cp_async_wait<CRING - 1>();  // chunk c has landed
       const int slot = c % CRING;
       const uint4 rr = rring[slot * 32];
-#pragma unroll 1
-      for (int hq = 0; hq < 2; hq++) {  // 4 columns: one residue word per subject
+      // two groups of 4 columns (one residue word per subject each); for
+      // T = 16 both are unrolled so the second group's profile loads can be
+      // issued during the first group's wavefront tail
+      auto group = [&](int hq) {
         const uint32_t wa = hq ? rr.y : rr.x;
         const uint32_t wb = hq ? rr.w : rr.z;
-#pragma unroll
-        for (int jp = 0; jp < 2; jp++) {
-          const int pair = hq * 2 + jp;
-          const uint4 b = bring[(slot * 4 + pair) * 32];
-          uint4 o;
-          packed_pair<T>(Hp, E, hdiag, smax, slice, p16, wa, wb, b, o, 2 * jp, GO2, NGE2, MGO,
-                         one);
-          if (!last) bd[(c * 4 + pair) * 32] = o;
+        const uint4 b0 = bring[(slot * 4 + 2 * hq) * 32];
+        const uint4 b1 = bring[(slot * 4 + 2 * hq + 1) * 32];
+        uint4 o0, o1;
+        packed_quad<T>(Hp, E, hdiag, smax, slice, p16, wa, wb, b0, b1, o0, o1, GO2, NGE2, MGO,
+                       one);
+        if (!last) {
+          bd[(c * 4 + 2 * hq) * 32] = o0;
+          bd[(c * 4 + 2 * hq + 1) * 32] = o1;
         }
+      };
+      if constexpr (T == 16) {
+        group(0);
+        group(1);
+      } else {
+#pragma unroll 1
+        for (int hq = 0; hq < 2; hq++) group(hq);
       }
     }
     cp_async_wait<0>();

@@ -35,7 +35,8 @@ class SwError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("rows_per_thread", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
                 ("long_cutoff", ctypes.c_int32), ("intra_rows", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("force_int32", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("force_int32", ctypes.c_int32),
+                ("auto_cutoff", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):

@@ -84,7 +84,7 @@ def test_long_sequences_full_size():
     pq, pd = sample_pairs(rng, len(w.queries), len(w.db), 6, w.planted)
     check_sample(got, w, pq, pd)
     # the packed inter-task path with int32 recompute agrees on every pair
-    packed = d.plan(len(w.queries), w.queries.total, long_cutoff=1 << 30)
+    packed = d.plan(len(w.queries), w.queries.total, long_cutoff=1 << 30, auto_cutoff=0)
     got2 = packed.search(w.queries.res, w.queries.lens, w.gap_open, w.gap_extend)
     assert packed.stats()["recomputed_pairs"] > 0
     assert (got2 == got).all()
