@@ -199,7 +199,7 @@ def run_reference(args):
     ms = 1e3 * statistics.mean(times)
     g = cells / (ms / 1e3) / 1e9
     out = {"impl": "reference", "metric": METRIC, "value": round(g, 4), "unit": "GCUPS",
-           "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
            "data": "synthetic",
            "config": {"workload": w.name, "sample": f"all {len(w.queries)} queries x first "

@@ -385,6 +385,7 @@ struct sw_plan {
   int32_t max_queries = 0;
   int64_t max_residues = 0;
   int32_t g_first = 0;      // first inter-task group under the cutoff
+  int32_t pair_blocks = 0;  // grid of the packed intra-task kernel
   // device buffers
   uint8_t* qres = nullptr;
   int64_t* qoff = nullptr;
@@ -429,6 +430,7 @@ static void plan_free(sw_plan* p) {
   cudaFree(p->scr.inter_border);
   cudaFree(p->scr.intra_border);
   cudaFree(p->scr.flags);
+  cudaFree(p->scr.pair_border);
   cudaFreeHost(p->params_h);
   cudaFreeHost(p->state_h);
   cudaFreeHost(p->qres_h);
@@ -489,12 +491,21 @@ extern "C" sw_status sw_plan_create(sw_db* db, int32_t max_queries, int64_t max_
   p->kc.blocks = dev_sms * bps;
   p->kc.smem = search_smem_bytes(o.rows_per_thread, o.intra_rows, o.warps_per_block);
   const int64_t W = (int64_t)p->kc.blocks * p->kc.warps;
+  const int pbps = pair_blocks_per_sm();
+  if (pbps < 1) {
+    plan_free(p);
+    return sw_set_error(SW_ECUDA, "packed intra-task kernel cannot launch");
+  }
+  p->pair_blocks = dev_sms * pbps;
+  const int64_t WP = (int64_t)p->pair_blocks * PAIR_WARPS;
 
   cudaError_t e = cudaSuccess;
   const int64_t nres = std::max<int64_t>(max_query_residues, 1);
   p->scr.inter_stride_vec = (int64_t)(L_inter / CHUNK) * 4 * 32;
   p->scr.intra_stride = std::max(v.max_len, 1);
+  p->scr.pair_stride = std::max(v.max_len, 1);
   p->scr.flag_capacity = (int64_t)max_queries * std::max<int64_t>(v.n, 1);
+  if (e == cudaSuccess) e = dalloc(&p->scr.pair_border, (size_t)(WP * p->scr.pair_stride));
   if (e == cudaSuccess) e = dalloc(&p->qres, nres);
   if (e == cudaSuccess) e = dalloc(&p->qoff, max_queries);
   if (e == cudaSuccess) e = dalloc(&p->qlen, max_queries);
@@ -542,6 +553,7 @@ static cudaError_t record(cudaEvent_t ev, cudaStream_t s, bool capturing) {
 static cudaError_t enqueue_kernels(sw_plan* p, cudaStream_t s, bool capturing) {
   cudaError_t e = cudaMemsetAsync(p->state, 0, sizeof(SearchState), s);
   if (e == cudaSuccess) e = record(p->ev[0], s, capturing);
+  if (e == cudaSuccess) e = launch_pairs(p->pair_blocks, p->db->view, p->params, p->state, p->scr, s);
   if (e == cudaSuccess) e = launch_search(p->kc, 0, p->db->view, p->params, p->state, p->scr, s);
   if (e == cudaSuccess) e = record(p->ev[1], s, capturing);
   if (e == cudaSuccess) e = launch_search(p->kc, 1, p->db->view, p->params, p->state, p->scr, s);
@@ -586,9 +598,13 @@ static sw_status plan_enqueue(sw_plan* p, const HostBatch& hb, int32_t nq, int32
   sw_status st = fill_scoring(P, gap_open, gap_extend, matrix, &packed_ok);
   if (st != SW_OK) return st;
   const DbView& v = p->db->view;
-  int32_t gf = packed_ok ? p->g_first : v.groups;
+  // packed: long subjects go to the packed intra-task kernel (subject pairs);
+  // otherwise (penalties too large for 16 bits, or forced) every subject
+  // goes to the int32 intra-task code
+  const bool packed = packed_ok && !p->opt.force_int32;
+  int32_t gf = packed ? p->g_first : v.groups;
   const double total_cells = (double)hb.total * (double)p->db->residues;
-  if (packed_ok && p->opt.auto_cutoff && total_cells >= kAutoCutoffMinCells) {
+  if (packed && p->opt.auto_cutoff && total_cells >= kAutoCutoffMinCells) {
     // Load balance: a (query, group) item is 64 subjects x the group length x
     // the query length.  Groups whose largest item exceeds a quarter of one
     // warp's share of the search go to the intra-task kernel instead, where
@@ -608,7 +624,8 @@ static sw_status plan_enqueue(sw_plan* p, const HostBatch& hb, int32_t nq, int32
   P.nq = nq;
   P.n_long = (int32_t)n_long;
   P.g_first = gf;
-  P.n_intra_items = n_long * nq;
+  P.n_intra_items = packed ? 0 : n_long * nq;
+  P.n_pair_items = packed ? (n_long + 1) / 2 * nq : 0;
   P.n_inter_items = (int64_t)(v.groups - gf) * nq;
   memcpy(p->qoff_h, hb.off.data(), sizeof(int64_t) * nq);
   memcpy(p->qlen_h, hb.len.data(), sizeof(int32_t) * nq);
@@ -627,8 +644,8 @@ static sw_status plan_enqueue(sw_plan* p, const HostBatch& hb, int32_t nq, int32
   int64_t qsum = hb.total;
   p->pending.cells = qsum * p->db->residues;
   p->pending.inter_items = P.n_inter_items;
-  p->pending.intra_items = P.n_intra_items;
-  p->pending.kernels_launched = 2;
+  p->pending.intra_items = n_long * nq;  // (query, long subject) pairs, packed or int32
+  p->pending.kernels_launched = 3;
   return SW_OK;
 }
 

@@ -50,7 +50,8 @@ __host__ __device__ inline int intpeak_ops_per_step(int op) {
 #define CHAINS 8
 
 template <int OP>
-__device__ __forceinline__ void step(uint32_t (&a)[CHAINS], uint32_t c0, uint32_t c1) {
+__device__ __forceinline__ void step(uint32_t (&a)[CHAINS], uint32_t c0, uint32_t c1,
+                                     uint32_t one) {
 #pragma unroll
   for (int i = 0; i < CHAINS; i++) {
     uint32_t x = a[i], y = a[(i + 1) % CHAINS];
@@ -69,7 +70,7 @@ __device__ __forceinline__ void step(uint32_t (&a)[CHAINS], uint32_t c0, uint32_
       asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(x), "r"(c1), "r"(y));
     } else if (OP == OP_CELL_BIASED) {
       // x: H' diag / F', y: profile source / E'; c0 = Go (both halves), c1 = -Ge
-      uint32_t p, t, one = c0 >> 31 | 1u;
+      uint32_t p, t;
       asm("prmt.b32 %0, %1, %2, 0xC480;" : "=r"(p) : "r"(y), "r"(x));
       uint32_t h = __viaddmax_s16x2(x, p, __vimax3_s16x2(y, x, c0));
       asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(t) : "r"(h), "r"(one), "r"(c1));
@@ -106,9 +107,10 @@ __global__ void intpeak_kernel(int iters, uint32_t seed, uint32_t* sink, long lo
 #pragma unroll
   for (int i = 0; i < CHAINS; i++) a[i] = seed * (threadIdx.x + 1) + i * 0x9E3779B9u;
   uint32_t c0 = seed ^ 0x00050005u, c1 = seed ^ 0x00020002u;
+  const uint32_t one = (seed >> 31) | 1u;  // 1, not known at compile time
   long long t0 = clock64();
   for (int it = 0; it < iters; it++) {
-    step<OP>(a, c0, c1);
+    step<OP>(a, c0, c1, one);
   }
   long long t1 = clock64();
   uint32_t acc = 0;

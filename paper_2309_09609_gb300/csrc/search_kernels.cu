@@ -552,6 +552,168 @@ cudaError_t launch_search(const KernelConfig& kc, int mode, const DbView& db,
   return cudaGetLastError();
 }
 
+// ---- packed intra-task kernel: one warp per pair of long subjects ----------
+// The two subjects of a pair are adjacent in length order, packed as the two
+// 16-bit halves of every word (the shorter one reads pad columns past its
+// end, which cannot raise its score).  Lane k owns PR query rows of a
+// 32*PR-row pass and updates column t - k at step t, receiving H' and F' of
+// row k*PR - 1 from lane k - 1 by __shfl_up_sync (Section II-B, intra-task
+// parallelism); lane 0 reads the previous pass's bottom row from this warp's
+// border scratch and lane 31 writes it (index t is read at step t and
+// rewritten at step t + 31).  Values carry the +Go bias of the inter-task
+// kernel, and a pair half whose S' reaches the threshold is recomputed in
+// int32 like any other saturated pair.
+constexpr int PR = 16;  // packed rows per lane (pair kernel)
+constexpr int PAIR_PROFILE = NCODES * 32 * PR;  // int8 [code][lane][PR]
+
+__global__ void __launch_bounds__(PAIR_WARPS * 32, 4)
+pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scratch scr) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  int8_t* sm = (int8_t*)smem;
+  for (int i = threadIdx.x; i < NCODES * NCODES; i += blockDim.x) sm[i] = P->sm[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  uint8_t* prof = smem + MATRIX_SMEM + wib * PAIR_PROFILE;
+  const int64_t warp_id = (int64_t)blockIdx.x * PAIR_WARPS + wib;
+  uint2* hb = scr.pair_border + warp_id * scr.pair_stride;
+  const int nq = P->nq;
+  if (nq <= 0) return;
+  const int64_t total = P->n_pair_items;
+  const int go = P->go;
+  const uint32_t GO2 = pack2(go), NGE2 = pack2(-P->ge);
+  const uint32_t MGO = (uint32_t)(-(int)((uint32_t)go * 65537u));
+  const uint32_t one = (uint32_t)P->one;
+  constexpr int ROWS = 32 * PR;
+  for (;;) {
+    unsigned long long it = 0;
+    if (lane == 0) it = atomicAdd(&st->pair_work, 1ull);
+    it = __shfl_sync(FULL, it, 0);
+    if ((int64_t)it >= total) break;
+    const int pair = (int)((int64_t)it / nq);
+    const int q = P->qorder[(int64_t)it % nq];
+    const int s0 = 2 * pair, s1 = 2 * pair + 1;
+    const bool has1 = s1 < P->n_long;
+    const int n0 = db.clen[s0], n1 = has1 ? db.clen[s1] : 0;  // n0 >= n1 (sorted)
+    const uint8_t* __restrict__ d0 = db.cont + db.coff[s0];
+    const uint8_t* __restrict__ d1 = has1 ? db.cont + db.coff[s1] : d0;
+    const int m = P->qlen[q];
+    const uint8_t* __restrict__ qr = P->qres + P->qoff[q];
+    const int npass = n0 > 0 ? (m + ROWS - 1) / ROWS : 0;
+    uint32_t smax = GO2;
+    for (int p = 0; p < npass; p++) {
+      __syncwarp();
+      {  // this lane's PR rows for every code
+        const int i0 = p * ROWS + lane * PR;
+        int qc[PR];
+#pragma unroll
+        for (int r = 0; r < PR; r++) qc[r] = (i0 + r < m) ? (int)qr[i0 + r] : -1;
+        for (int c = 0; c < NCODES; c++) {
+          uint32_t wv[PR / 4];
+#pragma unroll
+          for (int w = 0; w < PR / 4; w++) {
+            uint32_t acc = 0;
+#pragma unroll
+            for (int b = 0; b < 4; b++) {
+              const int r = w * 4 + b;
+              const int v = qc[r] >= 0 ? (int)sm[qc[r] * NCODES + c] : PAD_SCORE;
+              acc |= ((uint32_t)(uint8_t)(int8_t)v) << (8 * b);
+            }
+            wv[w] = acc;
+          }
+          *(uint4*)(prof + (c * 32 + lane) * PR) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+        }
+      }
+      __syncwarp();
+      uint32_t Hp[PR], E[PR];
+#pragma unroll
+      for (int r = 0; r < PR; r++) {
+        Hp[r] = GO2;  // H(i, 0) = 0
+        E[r] = 0u;    // E(i, 1) = -Go
+      }
+      uint32_t hdiag = GO2, out_h = GO2, out_f = 0u;
+      const bool last_pass = (p == npass - 1);
+      for (int t = 0; t < n0 + 31; t++) {
+        uint32_t in_h = __shfl_up_sync(FULL, out_h, 1);
+        uint32_t in_f = __shfl_up_sync(FULL, out_f, 1);
+        const int j = t - lane;
+        if (lane == 0) {
+          if (p > 0 && j < n0) {
+            const uint2 v = hb[j];
+            in_h = v.x;
+            in_f = v.y;
+          } else {
+            in_h = GO2;  // H(0, j) = 0
+            in_f = 0u;   // F(1, j) = -Go
+          }
+        }
+        if (j >= 0 && j < n0) {
+          const int c0 = d0[j];
+          const int c1 = j < n1 ? (int)d1[j] : PAD_CODE;
+          const uint4 pa = *(const uint4*)(prof + (c0 * 32 + lane) * PR);
+          const uint4 pb = *(const uint4*)(prof + (c1 * 32 + lane) * PR);
+          uint32_t hd = hdiag;
+          hdiag = in_h;
+          uint32_t f = in_f, hprev = 0;
+#pragma unroll
+          for (int r = 0; r < PR; r++) {
+            const int wq = r / 4;
+            const uint32_t a32 = wq == 0 ? pa.x : wq == 1 ? pa.y : wq == 2 ? pa.z : pa.w;
+            const uint32_t b32 = wq == 0 ? pb.x : wq == 1 ? pb.y : wq == 2 ? pb.z : pb.w;
+            uint32_t e = E[r];
+            const uint32_t h = packed_cell(hd, prmt(a32, b32, sext_pair_sel(r & 3)), e, f, GO2,
+                                           NGE2, MGO, one);
+            hd = Hp[r];
+            Hp[r] = h;
+            E[r] = e;
+            if (r & 1)
+              smax = __vimax3_s16x2(smax, hprev, h);
+            else
+              hprev = h;
+          }
+          out_h = Hp[PR - 1];
+          out_f = f;
+          if (lane == 31 && !last_pass) hb[j] = make_uint2(out_h, out_f);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) smax = __vmaxs2(smax, __shfl_xor_sync(FULL, smax, o));
+    if (lane < 2 && (lane == 0 || has1)) {
+      const int sidx = lane ? s1 : s0;
+      const int sb = (int)(int16_t)(lane ? (smax >> 16) : (smax & 0xffffu));  // S'
+      const int orig = db.perm[sidx];
+      if (orig >= 0) {
+        if (sb >= P->sat_threshold) {
+          const unsigned long long k = atomicAdd(&st->n_flags, 1ull);
+          if ((int64_t)k < scr.flag_capacity) scr.flags[k] = make_int2(q, sidx);
+        } else {
+          P->scores[(int64_t)q * db.n + orig] = sb - go;
+        }
+      }
+    }
+  }
+}
+
+size_t pair_smem_bytes() { return (size_t)MATRIX_SMEM + (size_t)PAIR_WARPS * PAIR_PROFILE; }
+
+int pair_blocks_per_sm() {
+  const size_t smem = pair_smem_bytes();
+  if (cudaFuncSetAttribute(pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return 0;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_kernel, PAIR_WARPS * 32, smem) !=
+      cudaSuccess)
+    return 0;
+  return nb;
+}
+
+cudaError_t launch_pairs(int blocks, const DbView& db, const SearchParams* params,
+                         SearchState* state, const Scratch& scr, cudaStream_t stream) {
+  pair_kernel<<<blocks, PAIR_WARPS * 32, pair_smem_bytes(), stream>>>(db, params, state, scr);
+  return cudaGetLastError();
+}
+
 // ---- plain int32 baseline: Algorithm 1, one launch per query ---------------
 constexpr int PT = 8;  // query rows per thread
 constexpr int NEG = -(1 << 28);

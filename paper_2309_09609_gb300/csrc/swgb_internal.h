@@ -54,8 +54,9 @@ struct SearchParams {
   const int32_t* qlen;    // [nq]
   const int32_t* qorder;  // [nq] query indices, longest first
   int32_t* scores;        // [nq x N] caller order
-  int64_t n_intra_items;  // n_long x nq  (int32 intra-task items)
+  int64_t n_intra_items;  // n_long x nq  (int32 intra-task items, when not packed)
   int64_t n_inter_items;  // inter groups x nq  (packed inter-task items)
+  int64_t n_pair_items;   // ceil(n_long / 2) x nq  (packed intra-task items: subject pairs)
   int32_t nq;
   int32_t n_long;         // sorted subjects [0, n_long) go to the intra-task kernel
   int32_t g_first;        // first inter-task group (n_long / GROUP)
@@ -71,6 +72,7 @@ struct SearchState {
   unsigned long long work;       // next work item (search kernel)
   unsigned long long n_flags;    // saturated pairs appended to the flag list
   unsigned long long recompute;  // next flag item (recompute kernel)
+  unsigned long long pair_work;  // next work item (packed intra-task kernel)
   unsigned int status;           // reserved: error bits raised on the device
   unsigned int pad;
 };
@@ -83,6 +85,8 @@ struct Scratch {
   int64_t intra_stride;       // int2 per warp
   int2* flags;                // saturated pairs: (query index, sorted subject index)
   int64_t flag_capacity;
+  uint2* pair_border;         // packed intra-task kernel, per warp: [column] (H', F') words
+  int64_t pair_stride;        // uint2 per warp
 };
 
 // ---- kernel launchers (search_kernels.cu) -------------------------------------
@@ -102,6 +106,13 @@ int search_blocks_per_sm(int rows, int intra_rows, int warps);
 cudaError_t launch_search(const KernelConfig& kc, int mode, const DbView& db,
                           const SearchParams* params, SearchState* state, const Scratch& scr,
                           cudaStream_t stream);
+
+// Packed intra-task kernel over subject pairs (long subjects).
+constexpr int PAIR_WARPS = 4;  // warps per block
+int pair_blocks_per_sm();
+size_t pair_smem_bytes();
+cudaError_t launch_pairs(int blocks, const DbView& db, const SearchParams* params,
+                         SearchState* state, const Scratch& scr, cudaStream_t stream);
 
 // Plain int32 baseline (Algorithm 1 per cell), one query per launch.
 int plain_blocks_per_sm();

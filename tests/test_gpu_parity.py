@@ -76,7 +76,33 @@ def test_long_subjects_intra_task(intra_rows):
     q = seqset(rng, [1, 31, 255, 256, 257, 300, 513, 700])
     res, st = all_paths(q, db, long_cutoff=64, intra_rows=intra_rows)
     assert st["intra_items"] > 0 and st["inter_items"] > 0
+    # and every subject through the int32 intra-task kernel (several passes)
+    d = swgb.Database.from_seqset(db)
+    res["int32_intra"] = d.plan(len(q), q.total, force_int32=1, intra_rows=intra_rows).search(
+        q.res, q.lens)
     assert_exact(res, oracle_all(q, db))
+
+
+def test_packed_pairs_odd_count_and_unequal_lengths():
+    # 65 long subjects: the last pair has one subject; pairs of unequal length
+    rng = np.random.default_rng(40)
+    db = seqset(rng, list(rng.integers(200, 2000, size=65)) + [7, 0, 150])
+    q = seqset(rng, [1, 100, 511, 512, 513, 1100])
+    res, st = all_paths(q, db, long_cutoff=100, plain=False)
+    assert st["intra_items"] >= 65 * len(q)
+    assert_exact(res, oracle_all(q, db))
+
+
+def test_saturation_through_the_pair_kernel():
+    rng = np.random.default_rng(41)
+    q = from_text("W" * 3100, "HEAGAWGHEE" * 30)
+    db = concat(from_text("W" * 2990, "W" * 3050 + "A" * 30, "W" * 2000),
+                seqset(rng, rng.integers(800, 3000, size=40)))
+    want = oracle_all(q, db)
+    assert want.max() > 32767
+    res, st = all_paths(q, db, long_cutoff=500, plain=False)
+    assert st["recomputed_pairs"] >= 2
+    assert_exact(res, want)
 
 
 def test_force_int32_everywhere():

@@ -74,8 +74,8 @@ def test_batched_uneven_full_size_autotuned():
 def test_long_sequences_full_size():
     w = synth.long_sequences(0)
     d = swgb.Database.from_seqset(w.db)
-    # the intra-task int32 warp-wavefront kernel for every subject
-    intra = d.plan(len(w.queries), w.queries.total, long_cutoff=0, intra_rows=16)
+    # the int32 intra-task warp-wavefront kernel for every subject
+    intra = d.plan(len(w.queries), w.queries.total, force_int32=1, intra_rows=16)
     got = intra.search(w.queries.res, w.queries.lens, w.gap_open, w.gap_extend)
     st = intra.stats()
     assert st["inter_items"] == 0 and st["intra_items"] == len(w.queries) * len(w.db)
@@ -83,8 +83,13 @@ def test_long_sequences_full_size():
     rng = np.random.default_rng(3)
     pq, pd = sample_pairs(rng, len(w.queries), len(w.db), 6, w.planted)
     check_sample(got, w, pq, pd)
-    # the packed inter-task path with int32 recompute agrees on every pair
-    packed = d.plan(len(w.queries), w.queries.total, long_cutoff=1 << 30, auto_cutoff=0)
-    got2 = packed.search(w.queries.res, w.queries.lens, w.gap_open, w.gap_extend)
-    assert packed.stats()["recomputed_pairs"] > 0
+    # the packed intra-task kernel (subject pairs) with int32 recompute
+    pairs = d.plan(len(w.queries), w.queries.total, long_cutoff=0)
+    got2 = pairs.search(w.queries.res, w.queries.lens, w.gap_open, w.gap_extend)
+    assert pairs.stats()["recomputed_pairs"] > 0 and pairs.stats()["inter_items"] == 0
     assert (got2 == got).all()
+    # the packed inter-task kernel with int32 recompute
+    packed = d.plan(len(w.queries), w.queries.total, long_cutoff=1 << 30, auto_cutoff=0)
+    got3 = packed.search(w.queries.res, w.queries.lens, w.gap_open, w.gap_extend)
+    assert packed.stats()["recomputed_pairs"] > 0
+    assert (got3 == got).all()
