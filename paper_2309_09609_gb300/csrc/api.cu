@@ -101,7 +101,7 @@ extern "C" void sw_options_default(sw_options* opt) {
   if (!opt) return;
   opt->rows_per_thread = 32;
   opt->warps_per_block = 8;
-  opt->long_cutoff = 7000;
+  opt->long_cutoff = 1500;
   opt->intra_rows = 8;
   opt->use_graph = 1;
   opt->force_int32 = 0;

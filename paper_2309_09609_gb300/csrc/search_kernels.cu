@@ -35,6 +35,8 @@
 // interaction is the atomic work counter, so nothing here can spin.
 #include <stdio.h>
 
+#include <type_traits>
+
 #include "swgb_internal.h"
 
 namespace swgb {
@@ -556,15 +558,27 @@ cudaError_t launch_search(const KernelConfig& kc, int mode, const DbView& db,
 // The two subjects of a pair are adjacent in length order, packed as the two
 // 16-bit halves of every word (the shorter one reads pad columns past its
 // end, which cannot raise its score).  Lane k owns PR query rows of a
-// 32*PR-row pass and updates column t - k at step t, receiving H' and F' of
-// row k*PR - 1 from lane k - 1 by __shfl_up_sync (Section II-B, intra-task
-// parallelism); lane 0 reads the previous pass's bottom row from this warp's
-// border scratch and lane 31 writes it (index t is read at step t and
-// rewritten at step t + 31).  Values carry the +Go bias of the inter-task
-// kernel, and a pair half whose S' reaches the threshold is recomputed in
-// int32 like any other saturated pair.
-constexpr int PR = 16;  // packed rows per lane (pair kernel)
+// 32*PR-row pass, split into PQ quarters of PQR rows; quarter q of lane k
+// updates column t - PQ*k - q at step t (Section II-B, intra-task
+// parallelism with neighbour border exchange):
+//   * quarter q needs the bottom row of quarter q - 1 at the same column
+//     (produced one step earlier) and its H' one column back (two steps
+//     earlier), so the PQ quarter updates of a step are independent;
+//   * quarter 0 receives the bottom row of lane k - 1 (its quarter PQ - 1,
+//     one step earlier) by __shfl_up_sync; lane 0 reads the previous pass's
+//     bottom row from this warp's border scratch and lane 31 writes it (index
+//     c is read at step c and rewritten at step c + 32*PQ - 1).
+// Residues are staged in a per-warp shared-memory ring 128 columns ahead;
+// quarter 0 loads the 16-byte profile row of its column and later quarters
+// reuse its words.  Values carry the +Go bias of the inter-task kernel, and a
+// pair half whose S' reaches the threshold is recomputed in int32 like any
+// other saturated pair.
+constexpr int PR = 16;                          // packed rows per lane
+constexpr int PQ = 4;                           // quarters (independent chains) per lane
+constexpr int PQR = PR / PQ;                    // rows per quarter
 constexpr int PAIR_PROFILE = NCODES * 32 * PR;  // int8 [code][lane][PR]
+constexpr int PRING = 384;                      // residue ring per subject: 3 blocks of 128
+constexpr int PAIR_SLICE = PAIR_PROFILE + 2 * PRING;
 
 __global__ void __launch_bounds__(PAIR_WARPS * 32, 4)
 pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scratch scr) {
@@ -573,7 +587,9 @@ pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scra
   for (int i = threadIdx.x; i < NCODES * NCODES; i += blockDim.x) sm[i] = P->sm[i];
   __syncthreads();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  uint8_t* prof = smem + MATRIX_SMEM + wib * PAIR_PROFILE;
+  uint8_t* prof = smem + MATRIX_SMEM + wib * PAIR_SLICE;
+  uint8_t* ring0 = prof + PAIR_PROFILE;
+  uint8_t* ring1 = ring0 + PRING;
   const int64_t warp_id = (int64_t)blockIdx.x * PAIR_WARPS + wib;
   uint2* hb = scr.pair_border + warp_id * scr.pair_stride;
   const int nq = P->nq;
@@ -599,6 +615,19 @@ pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scra
     const int m = P->qlen[q];
     const uint8_t* __restrict__ qr = P->qres + P->qoff[q];
     const int npass = n0 > 0 ? (m + ROWS - 1) / ROWS : 0;
+    // residues of columns [128 b, 128 b + 128) into ring slot b % 3 (pad past the end)
+    auto load_block = [&](int b) {
+      const int c = 128 * b + 4 * lane;
+      uint32_t w0 = 0, w1 = 0;
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        const int cc = c + i;
+        w0 |= (uint32_t)(cc < n0 ? d0[cc] : PAD_CODE) << (8 * i);
+        w1 |= (uint32_t)(cc < n1 ? d1[cc] : PAD_CODE) << (8 * i);
+      }
+      *(uint32_t*)(ring0 + c % PRING) = w0;
+      *(uint32_t*)(ring1 + c % PRING) = w1;
+    };
     uint32_t smax = GO2;
     for (int p = 0; p < npass; p++) {
       __syncwarp();
@@ -623,6 +652,7 @@ pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scra
           *(uint4*)(prof + (c * 32 + lane) * PR) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
         }
       }
+      load_block(0);
       __syncwarp();
       uint32_t Hp[PR], E[PR];
 #pragma unroll
@@ -630,15 +660,37 @@ pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scra
         Hp[r] = GO2;  // H(i, 0) = 0
         E[r] = 0u;    // E(i, 1) = -Go
       }
+      // quarter q's bottom-row H' one and two steps back, its F' one step back
+      uint32_t qh1[PQ], qh2[PQ], qf1[PQ];
+#pragma unroll
+      for (int k = 0; k < PQ; k++) {
+        qh1[k] = GO2;
+        qh2[k] = GO2;
+        qf1[k] = 0u;
+      }
+      // profile words of the last steps: h1 = words 1..3 one step back,
+      // h2 = words 2..3 two steps back, h3 = word 3 three steps back
+      uint32_t h1a[3] = {0, 0, 0}, h2a[2] = {0, 0}, h3a = 0;
+      uint32_t h1b[3] = {0, 0, 0}, h2b[2] = {0, 0}, h3b = 0;
       uint32_t hdiag = GO2, out_h = GO2, out_f = 0u;
       const bool last_pass = (p == npass - 1);
-      for (int t = 0; t < n0 + 31; t++) {
+      const int steps = n0 + 32 * PQ - 1;
+      int pos = (PRING - (PQ * lane) % PRING) % PRING;  // ring position of column t - PQ*lane
+      // one step of the wavefront; CHECK: some quarter may lie outside the
+      // columns (ramp-up and drain); in the steady state every quarter of
+      // every lane is inside, so the step needs no per-quarter test
+      auto step = [&](const int t, auto checked) {
+        constexpr bool CHECK = decltype(checked)::value;
+        if ((t & 127) == 0) {
+          load_block((t >> 7) + 1);
+          __syncwarp();
+        }
         uint32_t in_h = __shfl_up_sync(FULL, out_h, 1);
         uint32_t in_f = __shfl_up_sync(FULL, out_f, 1);
-        const int j = t - lane;
+        const int c0 = t - PQ * lane;  // quarter 0's column
         if (lane == 0) {
-          if (p > 0 && j < n0) {
-            const uint2 v = hb[j];
+          if (p > 0 && c0 < n0) {
+            const uint2 v = hb[c0];
             in_h = v.x;
             in_f = v.y;
           } else {
@@ -646,35 +698,77 @@ pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scra
             in_f = 0u;   // F(1, j) = -Go
           }
         }
-        if (j >= 0 && j < n0) {
-          const int c0 = d0[j];
-          const int c1 = j < n1 ? (int)d1[j] : PAD_CODE;
-          const uint4 pa = *(const uint4*)(prof + (c0 * 32 + lane) * PR);
-          const uint4 pb = *(const uint4*)(prof + (c1 * 32 + lane) * PR);
-          uint32_t hd = hdiag;
-          hdiag = in_h;
-          uint32_t f = in_f, hprev = 0;
+        // a ring slot not yet filled (this lane has not started) may hold any
+        // byte: clamp so the profile address stays inside this warp's slice
+        const int ra = min((int)ring0[pos], PAD_CODE), rb = min((int)ring1[pos], PAD_CODE);
+        pos = pos + 1 == PRING ? 0 : pos + 1;
+        const uint4 pa = *(const uint4*)(prof + (ra * 32 + lane) * PR);
+        const uint4 pb = *(const uint4*)(prof + (rb * 32 + lane) * PR);
+        const uint32_t wa[PQ] = {pa.x, h1a[0], h2a[0], h3a};
+        const uint32_t wb[PQ] = {pb.x, h1b[0], h2b[0], h3b};
+        uint32_t nh[PQ], nf[PQ];
 #pragma unroll
-          for (int r = 0; r < PR; r++) {
-            const int wq = r / 4;
-            const uint32_t a32 = wq == 0 ? pa.x : wq == 1 ? pa.y : wq == 2 ? pa.z : pa.w;
-            const uint32_t b32 = wq == 0 ? pb.x : wq == 1 ? pb.y : wq == 2 ? pb.z : pb.w;
-            uint32_t e = E[r];
-            const uint32_t h = packed_cell(hd, prmt(a32, b32, sext_pair_sel(r & 3)), e, f, GO2,
-                                           NGE2, MGO, one);
-            hd = Hp[r];
-            Hp[r] = h;
-            E[r] = e;
-            if (r & 1)
-              smax = __vimax3_s16x2(smax, hprev, h);
-            else
-              hprev = h;
+        for (int k = 0; k < PQ; k++) {
+          const int col = c0 - k;
+          bool active = true;
+          if constexpr (CHECK) active = col >= 0 && col < n0;
+          nh[k] = qh1[k];
+          nf[k] = qf1[k];
+          if (active) {
+            uint32_t hd = k == 0 ? hdiag : qh2[k - 1];  // H' one row up, one column back
+            uint32_t f = k == 0 ? in_f : qf1[k - 1];    // F' of this quarter's first row
+            uint32_t hprev = 0;
+#pragma unroll
+            for (int i = 0; i < PQR; i++) {
+              const int r = k * PQR + i;
+              uint32_t e = E[r];
+              const uint32_t h = packed_cell(hd, prmt(wa[k], wb[k], sext_pair_sel(i)), e, f, GO2,
+                                             NGE2, MGO, one);
+              hd = Hp[r];
+              Hp[r] = h;
+              E[r] = e;
+              if (i & 1)
+                smax = __vimax3_s16x2(smax, hprev, h);
+              else
+                hprev = h;
+            }
+            nh[k] = Hp[k * PQR + PQR - 1];
+            nf[k] = f;
+            if (k == PQ - 1 && lane == 31 && !last_pass) hb[col] = make_uint2(nh[k], f);
+          } else if (col < 0) {
+            nh[k] = GO2;  // left of the matrix: H = 0
           }
-          out_h = Hp[PR - 1];
-          out_f = f;
-          if (lane == 31 && !last_pass) hb[j] = make_uint2(out_h, out_f);
         }
-      }
+        hdiag = in_h;
+        out_h = nh[PQ - 1];
+        out_f = nf[PQ - 1];
+#pragma unroll
+        for (int k = 0; k < PQ; k++) {
+          qh2[k] = qh1[k];
+          qh1[k] = nh[k];
+          qf1[k] = nf[k];
+        }
+        h3a = h2a[1];
+        h2a[0] = h1a[1];
+        h2a[1] = h1a[2];
+        h1a[0] = pa.y;
+        h1a[1] = pa.z;
+        h1a[2] = pa.w;
+        h3b = h2b[1];
+        h2b[0] = h1b[1];
+        h2b[1] = h1b[2];
+        h1b[0] = pb.y;
+        h1b[1] = pb.z;
+        h1b[2] = pb.w;
+      };
+      // every quarter of every lane is inside the columns for 32*PQ-1 <= t < n0
+      const int ramp = steps < 32 * PQ - 1 ? steps : 32 * PQ - 1;
+      const int steady_end = n0 > ramp ? n0 : ramp;
+      int t = 0;
+      for (; t < ramp; t++) step(t, std::true_type{});
+#pragma unroll 4
+      for (; t < steady_end; t++) step(t, std::false_type{});
+      for (; t < steps; t++) step(t, std::true_type{});
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) smax = __vmaxs2(smax, __shfl_xor_sync(FULL, smax, o));
@@ -694,7 +788,7 @@ pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scra
   }
 }
 
-size_t pair_smem_bytes() { return (size_t)MATRIX_SMEM + (size_t)PAIR_WARPS * PAIR_PROFILE; }
+size_t pair_smem_bytes() { return (size_t)MATRIX_SMEM + (size_t)PAIR_WARPS * PAIR_SLICE; }
 
 int pair_blocks_per_sm() {
   const size_t smem = pair_smem_bytes();
