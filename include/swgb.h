@@ -113,8 +113,11 @@ typedef struct {
   int64_t recomputed_pairs;  /* pairs whose 16-bit score saturated, redone in int32 */
   int32_t timed_out;         /* 1 if a bounded device wait gave up */
   int32_t kernels_launched;  /* kernels of this library launched by the search */
-  float search_ms;           /* device time of the persistent search kernel (CUDA events) */
+  float search_ms;           /* device time of the inter-task search kernel (CUDA events) */
   float recompute_ms;        /* device time of the int32 recompute kernel (CUDA events) */
+  float pair_ms;             /* device time of the packed intra-task kernel (CUDA events) */
+  int32_t pad_;
+  int64_t inter_cells;       /* cells scored by the inter-task kernel */
 } sw_stats;
 
 /* Creates a search context for up to max_queries queries holding up to

@@ -158,6 +158,7 @@ struct sw_db {
   DbView view{};
   std::vector<int32_t> glen_h;   // padded group lengths (host copy)
   std::vector<int32_t> clen_h;   // sorted lengths (host copy)
+  std::vector<int64_t> cres_h;   // [N + 1] residues of sorted subjects [0, s)
   int64_t residues = 0;
   // owned device buffers
   uint8_t* inter = nullptr;
@@ -280,6 +281,8 @@ extern "C" sw_status sw_db_create(const uint8_t* residues, const int32_t* length
   db->view.groups = G;
   db->view.max_len = max_len;
   db->glen_h = std::move(glen);
+  db->cres_h.assign((size_t)N + 1, 0);
+  for (int64_t s = 0; s < N; s++) db->cres_h[s + 1] = db->cres_h[s] + clen[s];
   db->clen_h = std::move(clen);
   *out = db;
   return SW_OK;
@@ -405,7 +408,8 @@ struct sw_plan {
   // graph
   cudaGraphExec_t graph = nullptr;
   cudaEvent_t done = nullptr;
-  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // before search, after search, after recompute
+  // before the pair kernel, before and after the inter-task kernel, after recompute
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   bool in_flight = false;
   sw_stats stats{};
   sw_stats pending{};
@@ -554,10 +558,11 @@ static cudaError_t enqueue_kernels(sw_plan* p, cudaStream_t s, bool capturing) {
   cudaError_t e = cudaMemsetAsync(p->state, 0, sizeof(SearchState), s);
   if (e == cudaSuccess) e = record(p->ev[0], s, capturing);
   if (e == cudaSuccess) e = launch_pairs(p->pair_blocks, p->db->view, p->params, p->state, p->scr, s);
-  if (e == cudaSuccess) e = launch_search(p->kc, 0, p->db->view, p->params, p->state, p->scr, s);
   if (e == cudaSuccess) e = record(p->ev[1], s, capturing);
-  if (e == cudaSuccess) e = launch_search(p->kc, 1, p->db->view, p->params, p->state, p->scr, s);
+  if (e == cudaSuccess) e = launch_search(p->kc, 0, p->db->view, p->params, p->state, p->scr, s);
   if (e == cudaSuccess) e = record(p->ev[2], s, capturing);
+  if (e == cudaSuccess) e = launch_search(p->kc, 1, p->db->view, p->params, p->state, p->scr, s);
+  if (e == cudaSuccess) e = record(p->ev[3], s, capturing);
   return e;
 }
 
@@ -645,16 +650,18 @@ static sw_status plan_enqueue(sw_plan* p, const HostBatch& hb, int32_t nq, int32
   p->pending.cells = qsum * p->db->residues;
   p->pending.inter_items = P.n_inter_items;
   p->pending.intra_items = n_long * nq;  // (query, long subject) pairs, packed or int32
+  p->pending.inter_cells = qsum * (p->db->residues - p->db->cres_h[n_long]);
   p->pending.kernels_launched = 3;
   return SW_OK;
 }
 
 static void finish_stats(sw_plan* p) {
   p->stats = p->pending;
-  if (cudaEventElapsedTime(&p->stats.search_ms, p->ev[0], p->ev[1]) != cudaSuccess ||
-      cudaEventElapsedTime(&p->stats.recompute_ms, p->ev[1], p->ev[2]) != cudaSuccess) {
+  if (cudaEventElapsedTime(&p->stats.pair_ms, p->ev[0], p->ev[1]) != cudaSuccess ||
+      cudaEventElapsedTime(&p->stats.search_ms, p->ev[1], p->ev[2]) != cudaSuccess ||
+      cudaEventElapsedTime(&p->stats.recompute_ms, p->ev[2], p->ev[3]) != cudaSuccess) {
     cudaGetLastError();
-    p->stats.search_ms = p->stats.recompute_ms = -1.f;
+    p->stats.pair_ms = p->stats.search_ms = p->stats.recompute_ms = -1.f;
   }
   p->stats.recomputed_pairs = (int64_t)std::min<unsigned long long>(
       p->state_h->n_flags, (unsigned long long)p->scr.flag_capacity);

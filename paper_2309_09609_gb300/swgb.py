@@ -43,7 +43,9 @@ class Stats(ctypes.Structure):
     _fields_ = [("cells", ctypes.c_int64), ("inter_items", ctypes.c_int64),
                 ("intra_items", ctypes.c_int64), ("recomputed_pairs", ctypes.c_int64),
                 ("timed_out", ctypes.c_int32), ("kernels_launched", ctypes.c_int32),
-                ("search_ms", ctypes.c_float), ("recompute_ms", ctypes.c_float)]
+                ("search_ms", ctypes.c_float), ("recompute_ms", ctypes.c_float),
+                ("pair_ms", ctypes.c_float), ("pad_", ctypes.c_int32),
+                ("inter_cells", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
