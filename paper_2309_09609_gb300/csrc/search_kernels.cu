@@ -668,22 +668,31 @@ pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scra
         qh2[k] = GO2;
         qf1[k] = 0u;
       }
-      // profile words of the last steps: h1 = words 1..3 one step back,
-      // h2 = words 2..3 two steps back, h3 = word 3 three steps back
-      uint32_t h1a[3] = {0, 0, 0}, h2a[2] = {0, 0}, h3a = 0;
-      uint32_t h1b[3] = {0, 0, 0}, h2b[2] = {0, 0}, h3b = 0;
+      // profile vectors of the last four steps in slot (t mod 4): quarter q at
+      // step t uses word q of the vector loaded at step t - q; steps run in
+      // blocks of four so every slot index is a compile-time constant
+      uint4 VA[PQ], VB[PQ];
+#pragma unroll
+      for (int k = 0; k < PQ; k++) {
+        VA[k] = make_uint4(0u, 0u, 0u, 0u);
+        VB[k] = make_uint4(0u, 0u, 0u, 0u);
+      }
       uint32_t hdiag = GO2, out_h = GO2, out_f = 0u;
       const bool last_pass = (p == npass - 1);
       const int steps = n0 + 32 * PQ - 1;
-      int pos = (PRING - (PQ * lane) % PRING) % PRING;  // ring position of column t - PQ*lane
+      // ring position of column t0 - PQ*lane; a multiple of 4, as is PRING
+      int pos = (PRING - (PQ * lane) % PRING) % PRING;
       // one step of the wavefront; CHECK: some quarter may lie outside the
       // columns (ramp-up and drain); in the steady state every quarter of
       // every lane is inside, so the step needs no per-quarter test
-      auto step = [&](const int t, auto checked) {
+      auto step = [&](const int t, auto checked, auto slot) {
         constexpr bool CHECK = decltype(checked)::value;
-        if ((t & 127) == 0) {
-          load_block((t >> 7) + 1);
-          __syncwarp();
+        constexpr int U = decltype(slot)::value;  // t mod 4
+        if constexpr (U == 0) {
+          if ((t & 127) == 0) {
+            load_block((t >> 7) + 1);
+            __syncwarp();
+          }
         }
         uint32_t in_h = __shfl_up_sync(FULL, out_h, 1);
         uint32_t in_f = __shfl_up_sync(FULL, out_f, 1);
@@ -700,12 +709,12 @@ pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scra
         }
         // a ring slot not yet filled (this lane has not started) may hold any
         // byte: clamp so the profile address stays inside this warp's slice
-        const int ra = min((int)ring0[pos], PAD_CODE), rb = min((int)ring1[pos], PAD_CODE);
-        pos = pos + 1 == PRING ? 0 : pos + 1;
-        const uint4 pa = *(const uint4*)(prof + (ra * 32 + lane) * PR);
-        const uint4 pb = *(const uint4*)(prof + (rb * 32 + lane) * PR);
-        const uint32_t wa[PQ] = {pa.x, h1a[0], h2a[0], h3a};
-        const uint32_t wb[PQ] = {pb.x, h1b[0], h2b[0], h3b};
+        const int ra = min((int)ring0[pos + U], PAD_CODE);
+        const int rb = min((int)ring1[pos + U], PAD_CODE);
+        VA[U] = *(const uint4*)(prof + (ra * 32 + lane) * PR);
+        VB[U] = *(const uint4*)(prof + (rb * 32 + lane) * PR);
+        const uint32_t wa[PQ] = {VA[U].x, VA[(U + 3) & 3].y, VA[(U + 2) & 3].z, VA[(U + 1) & 3].w};
+        const uint32_t wb[PQ] = {VB[U].x, VB[(U + 3) & 3].y, VB[(U + 2) & 3].z, VB[(U + 1) & 3].w};
         uint32_t nh[PQ], nf[PQ];
 #pragma unroll
         for (int k = 0; k < PQ; k++) {
@@ -748,27 +757,21 @@ pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scra
           qh1[k] = nh[k];
           qf1[k] = nf[k];
         }
-        h3a = h2a[1];
-        h2a[0] = h1a[1];
-        h2a[1] = h1a[2];
-        h1a[0] = pa.y;
-        h1a[1] = pa.z;
-        h1a[2] = pa.w;
-        h3b = h2b[1];
-        h2b[0] = h1b[1];
-        h2b[1] = h1b[2];
-        h1b[0] = pb.y;
-        h1b[1] = pb.z;
-        h1b[2] = pb.w;
       };
-      // every quarter of every lane is inside the columns for 32*PQ-1 <= t < n0
-      const int ramp = steps < 32 * PQ - 1 ? steps : 32 * PQ - 1;
-      const int steady_end = n0 > ramp ? n0 : ramp;
-      int t = 0;
-      for (; t < ramp; t++) step(t, std::true_type{});
-#pragma unroll 4
-      for (; t < steady_end; t++) step(t, std::false_type{});
-      for (; t < steps; t++) step(t, std::true_type{});
+      auto block = [&](const int t0, auto checked) {
+        step(t0, checked, std::integral_constant<int, 0>{});
+        step(t0 + 1, checked, std::integral_constant<int, 1>{});
+        step(t0 + 2, checked, std::integral_constant<int, 2>{});
+        step(t0 + 3, checked, std::integral_constant<int, 3>{});
+        pos = pos + 4 == PRING ? 0 : pos + 4;
+      };
+      // every quarter of every lane is inside the columns for 32*PQ-1 <= t < n0;
+      // the last block may run past `steps`, where every quarter is outside
+      int t0 = 0;
+      for (; t0 < 32 * PQ; t0 += 4) block(t0, std::true_type{});
+#pragma unroll 1
+      for (; t0 + 4 <= n0; t0 += 4) block(t0, std::false_type{});
+      for (; t0 < steps; t0 += 4) block(t0, std::true_type{});
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) smax = __vmaxs2(smax, __shfl_xor_sync(FULL, smax, o));
