@@ -6,13 +6,14 @@ synthetic database of 570,000 subjects with lognormal lengths (mean 360,
 paper's search (Section IV-A), synthetic because Env-NR is not available.
 
 One step = one exact search of all queries against the whole database
-through a plan (persistent packed 16-bit kernel + int32 long-subject and
-recompute work, replayed from a CUDA graph).  Printed: one JSON line with
-GCUPS (cells = sum of query lengths x sum of subject lengths), per-step
-latency p50/p99, the plain int32 one-query-per-launch baseline, the integer
-roofline of the search kernel against the intpeak microbenchmark, the end-to-
-end rate through the C ABI with host buffers, and the CPU oracle timed on a
-bounded sample on the host cores.
+through a plan: the packed pair kernel (long subjects), the packed inter-task
+kernel (the rest) and the int32 intra-task kernel (saturated pairs), replayed
+from a CUDA graph.  Printed: one JSON line with GCUPS (cells = sum of query
+lengths x sum of subject lengths), per-step latency p50/p99, the plain int32
+one-query-per-launch baseline, the integer roofline of the dominant kernel
+against the intpeak microbenchmark, the end-to-end rate through the C ABI
+with host buffers, and the CPU oracle timed on a bounded sample on the host
+cores.
 
 ``--impl reference`` times the CPU oracle instead (the reference arm).
 """
@@ -36,6 +37,13 @@ sys.path.insert(0, ROOT)
 METRIC = "GCUPS on 1 GB300 (batched packed vs plain int32), bit-exact scores; p50/p99 latency"
 WORKLOADS = ("paper-search", "plain-small", "batched-uneven", "long")
 
+# CPU oracle sample budgets (cells): the baseline leg, and one reference-arm
+# step.  On 16 Arm cores the oracle scored the long-sequence pairs at
+# 0.5-0.8 GCUPS and the short-subject workloads at 8.3-8.5, hence the smaller
+# budget.
+CPU_CELLS = {"paper-search": 1e11, "batched-uneven": 1e11, "plain-small": 1e11, "long": 1e10}
+REF_CELLS = {"paper-search": 1.5e10, "batched-uneven": 1.5e10, "plain-small": 1.5e10, "long": 2e9}
+
 # algorithmic ALU-pipe lane-operations per cell of the packed recurrence: per
 # 32-bit word (2 cells) one prmt (profile pair), vimax3 (E', F', Go), viaddmax
 # (H'), viaddmax (E' next column), viaddmax (F' next row) and half a vimax3 (S);
@@ -54,8 +62,12 @@ def parse():
     ap.add_argument("--rows", type=int, default=None, help="packed rows per thread (16/32)")
     ap.add_argument("--cutoff", type=int, default=None, help="inter/intra length cutoff")
     ap.add_argument("--warps", type=int, default=None)
-    ap.add_argument("--cpu-sample", type=float, default=0.01,
-                    help="fraction of subjects the CPU oracle baseline searches")
+    ap.add_argument("--cpu-cells", type=float, default=None,
+                    help="cell budget of the CPU oracle baseline's sample (all queries x the "
+                         "first subjects that fit); default per workload, 10-30 s on 16 cores")
+    ap.add_argument("--ref-cells", type=float, default=None,
+                    help="cell budget of one reference-arm step (the CPU oracle); default per "
+                         "workload, a few seconds")
     ap.add_argument("--subjects", type=int, default=None,
                     help="shrink the database (profiling / small cases)")
     ap.add_argument("--queries", type=int, default=None, help="keep only N queries")
@@ -159,11 +171,12 @@ def max_over_ranks(x, dist, device):
     return float(t.item())
 
 
-def oracle_sample(w, frac, seed=0):
-    """All queries vs the first `frac` of subjects (by caller index)."""
-    n = max(1, int(round(frac * len(w.db))))
-    sub = w.db.subset(np.arange(n))
-    return sub
+def oracle_sample(w, cell_budget):
+    """All queries vs the longest prefix of subjects (by caller index, which is
+    random with respect to length) whose cells fit `cell_budget`; at least one."""
+    per = np.cumsum(w.db.lens.astype(np.int64)) * int(w.queries.total)
+    n = max(1, int(np.searchsorted(per, cell_budget, side="right")))
+    return w.db.subset(np.arange(n))
 
 
 def time_oracle(w, sub, nthreads):
@@ -187,8 +200,7 @@ def run_reference(args):
     import oracle
     oracle.build()
     w = make_workload(args.workload, args.seed, args.subjects, args.queries, args.query_offset)
-    frac = min(args.cpu_sample, 0.002) if args.workload == "paper-search" else args.cpu_sample
-    sub = oracle_sample(w, frac)
+    sub = oracle_sample(w, args.ref_cells or REF_CELLS[args.workload])
     cores = os.cpu_count() or 1
     for _ in range(args.warmup):
         time_oracle(w, sub, cores)
@@ -211,28 +223,40 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "search_kernel_paper-search_traffic.txt")
-KERNEL_SOURCE = os.path.join(ROOT, "paper_2309_09609_gb300", "csrc", "search_kernels.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "inter_kernel_paper-search_traffic.txt")
+# the inter-task kernel's own sources: its file and the device helpers it includes
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2309_09609_gb300", "csrc", f)
+                  for f in ("inter_kernel.cu", "device_common.cuh")]
+
+
+def kernel_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def traffic_record():
+    rec = {}
+    if os.path.exists(TRAFFIC_FILE):
+        with open(TRAFFIC_FILE) as fh:
+            for line in fh:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    rec[k.strip()] = v.strip()
+    return rec
 
 
 def profiled_traffic(args):
     """DRAM bytes per launch of the inter-task kernel from the committed ncu
-    record, if it covers this workload and the kernel source is unchanged."""
-    import hashlib
+    record, if it covers this workload and the kernel's sources are unchanged."""
     default = (args.workload == "paper-search" and not args.subjects and not args.queries
                and args.rows in (None, 32) and args.warps in (None, 8)
                and args.cutoff in (None, 1500) and not args.tune)
-    if not default or not os.path.exists(TRAFFIC_FILE):
-        return None
-    rec = {}
-    with open(TRAFFIC_FILE) as fh:
-        for line in fh:
-            if ":" in line and not line.startswith("#"):
-                k, v = line.split(":", 1)
-                rec[k.strip()] = v.strip()
-    with open(KERNEL_SOURCE, "rb") as fh:
-        sha = hashlib.sha256(fh.read()).hexdigest()
-    if sha != rec.get("kernel_source_sha256"):
+    rec = traffic_record()
+    if not default or rec.get("kernel_sources_sha256") != kernel_sources_sha256():
         return None
     return int(rec["dram_bytes_per_launch"])
 
@@ -355,27 +379,37 @@ def run_native(args):
               "gpu_launches": stats["kernels_launched"] * args.steps,
               "clocks": clocks}
 
-    # roofline of the dominant kernel (the inter-task search kernel): ALU-pipe
-    # lane-ops vs the intpeak microbenchmark's measured DPX throughput
-    # (SMs x clock x per-SM rate); cells = those that kernel scored
-    kms = statistics.mean(kernel_ms) if kernel_ms else float("nan")
-    inter_cells = stats["inter_cells"]
-    achieved = PACKED_ALU_OPS_PER_CELL * inter_cells / (kms / 1e3) / 1e12
+    # roofline of the dominant kernel: ALU-pipe lane-ops vs the intpeak
+    # microbenchmark's measured DPX throughput (SMs x clock x per-SM rate).
+    # The inter-task kernel scores the short subjects' cells, the packed pair
+    # kernel the rest (subjects longer than the cutoff); both run the same
+    # packed recurrence, so both count the same lane-ops per cell.
     sms = torch.cuda.get_device_properties(device).multi_processor_count
     rate, rate_mhz, _ = swgb.intpeak("viaddmax_s16x2", 8, 256, 20000)
     max_mhz = clocks.get("sm_max_mhz") or 2070.0
     peak = rate * sms * max_mhz * 1e6 / 1e12
-    result["roofline"] = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
-                          "unit": "Tops/s", "frac": round(achieved / peak, 4),
-                          "traffic": profiled_traffic(args),
-                          "kernel": "search_kernel (mode 0, inter-task)", "kernel_ms": round(kms, 3),
-                          "kernel_cells": inter_cells,
-                          "pair_kernel_ms": round(statistics.mean(pair_ms), 3),
+    per_kernel = {}
+    for name, kcells, kms_list in (
+            ("inter_kernel (packed inter-task)", stats["inter_cells"], kernel_ms),
+            ("pair_kernel (packed intra-task)", stats["cells"] - stats["inter_cells"], pair_ms)):
+        kms = statistics.mean(kms_list) if kms_list else float("nan")
+        ach = PACKED_ALU_OPS_PER_CELL * kcells / (kms / 1e3) / 1e12 if kcells else 0.0
+        per_kernel[name] = {"ms": round(kms, 3), "cells": int(kcells), "achieved": round(ach, 3),
+                            "frac": round(ach / peak, 4)}
+    dominant = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
+    dom = per_kernel[dominant]
+    inter = dominant.startswith("inter_kernel")
+    result["roofline"] = {"bound": "alu", "achieved": dom["achieved"], "peak": round(peak, 3),
+                          "unit": "Tops/s", "frac": dom["frac"],
+                          "traffic": profiled_traffic(args) if inter else None,
+                          "kernel": dominant, "kernel_ms": dom["ms"], "kernel_cells": dom["cells"],
+                          "kernels": per_kernel,
                           "alu_ops_per_cell": PACKED_ALU_OPS_PER_CELL,
                           "peak_source": f"intpeak viaddmax_s16x2 {rate:.1f} lane-ops/clk/SM x "
                                          f"{sms} SMs x {max_mhz:.0f} MHz (max SM clock), measured",
                           "intpeak_clock_mhz": round(rate_mhz, 1),
                           "peak_gcups": round(peak * 1e12 / PACKED_ALU_OPS_PER_CELL / 1e9, 1),
+                          "pair_kernel_ms": per_kernel["pair_kernel (packed intra-task)"]["ms"],
                           "recompute_ms": round(statistics.mean(recompute_ms), 3)}
 
     # plain int32 one-query-per-launch baseline on the same workload
@@ -418,7 +452,7 @@ def run_native(args):
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
         oracle.build()
-        sub = oracle_sample(w, args.cpu_sample)
+        sub = oracle_sample(w, args.cpu_cells or CPU_CELLS[args.workload])
         cores = os.cpu_count() or 1
         ref, ocells, odt = time_oracle(w, sub, cores)
         got = out_host.numpy()[:, :len(sub)]

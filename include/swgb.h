@@ -94,7 +94,7 @@ typedef struct {
   int32_t rows_per_thread;   /* query rows per thread in the packed inter-task kernel: 16 or 32 */
   int32_t warps_per_block;   /* 4 or 8 */
   int32_t long_cutoff;       /* subjects longer than this use the intra-task kernel */
-  int32_t intra_rows;        /* query rows per lane in the intra-task kernel: 8 or 16 */
+  int32_t intra_rows;        /* query rows per lane in the int32 intra-task kernel: 8 or 16 */
   int32_t use_graph;         /* 1: capture the launch sequence in a CUDA graph */
   int32_t force_int32;       /* 1: all subjects through the int32 intra-task kernel */
   int32_t auto_cutoff;       /* 1: per search of >= 1e10 cells, also send to the intra-task
@@ -114,7 +114,9 @@ typedef struct {
   int32_t timed_out;         /* 1 if a bounded device wait gave up */
   int32_t kernels_launched;  /* kernels of this library launched by the search */
   float search_ms;           /* device time of the inter-task search kernel (CUDA events) */
-  float recompute_ms;        /* device time of the int32 recompute kernel (CUDA events) */
+  float recompute_ms;        /* device time of the int32 intra-task kernel (CUDA events):
+                                the recompute of saturated pairs, or every pair when the
+                                packed path is off */
   float pair_ms;             /* device time of the packed intra-task kernel (CUDA events) */
   int32_t pad_;
   int64_t inter_cells;       /* cells scored by the inter-task kernel */
@@ -131,11 +133,15 @@ sw_status sw_plan_create(sw_db* db, int32_t max_queries, int64_t max_query_resid
 void sw_plan_destroy(sw_plan* plan);
 
 /* Exact scores of every query against every subject (Eq. 1-3), the batched
- * path: one persistent launch over all (query, subject-group) work items,
- * longest first, scored as packed 16-bit pairs (two subjects per 32-bit
- * word) with every pair whose 16-bit score may have saturated recomputed in
- * int32, plus long subjects in the int32 intra-task kernel; the launch
- * sequence is replayed from a CUDA graph when opt.use_graph is set.
+ * path: three persistent launches, each taking its work longest first from
+ * an atomic counter -- the packed intra-task kernel over pairs of subjects
+ * longer than opt.long_cutoff, the packed inter-task kernel over (query,
+ * group of 64 subjects) items, both scoring two subjects per 32-bit word in
+ * 16 bits, and the int32 intra-task kernel, which recomputes every pair whose
+ * 16-bit score may have saturated (one block per pair).  With gap penalties
+ * too large for 16 bits, or opt.force_int32, every pair goes to the int32
+ * kernel instead.  The launch sequence is replayed from a CUDA graph when
+ * opt.use_graph is set.
  *   queries:   concatenated query codes (sum(q_lengths) bytes), host or device.
  *   q_lengths: n_queries int32, host or device.
  *   scores:    n_queries x n_subjects int32, host or device, written in full.
@@ -216,7 +222,9 @@ sw_status sw_search_pairs_noalloc(const uint8_t* queries, const int64_t* q_offse
  * 1 imax, 2 viaddmax_s32, 3 viaddmax_s16x2, 4 viaddmax_s16x2_relu,
  * 5 vimax3_s16x2, 6 vmaxs2, 7 vsub2, 8 vaddss2, 9 prmt, 10 packed cell pair,
  * 11 packed cell pair + prmt, 12 int32 cell, 13 imad, 14 the biased packed
- * cell pair of the search kernel); results (host memory):
+ * cell pair of the search kernel, 15 vadd4, 16 vmaxu4, 17 vmaxs4, 18 vaddus4,
+ * 19 vsubus4, 20 an unsigned biased 8x4 cell update of four cells, 10 ops);
+ * results (host memory):
  * out[0] lane-operations per SM clock, out[1] SM clock in MHz, out[2] seconds. */
 sw_status sw_intpeak(int32_t op, int32_t blocks_per_sm, int32_t threads, int32_t iters,
                      double* out);

@@ -384,7 +384,8 @@ static sw_status fill_scoring(SearchParams& P, int32_t gap_open, int32_t gap_ext
 struct sw_plan {
   sw_db* db = nullptr;
   sw_options opt{};
-  KernelConfig kc{};
+  KernelConfig kc{};        // inter-task kernel
+  KernelConfig ikc{};       // int32 intra-task kernel
   int32_t max_queries = 0;
   int64_t max_residues = 0;
   int32_t g_first = 0;      // first inter-task group under the cutoff
@@ -483,18 +484,28 @@ extern "C" sw_status sw_plan_create(sw_db* db, int32_t max_queries, int64_t max_
 
   int dev_sms = 0;
   cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, db->device);
-  const int bps = search_blocks_per_sm(o.rows_per_thread, o.intra_rows, o.warps_per_block);
+  const int bps = inter_blocks_per_sm(o.rows_per_thread, o.warps_per_block);
   if (bps < 1) {
     plan_free(p);
-    return sw_set_error(SW_ECUDA, "search kernel cannot launch with %d warps (rows %d/%d)",
-                        o.warps_per_block, o.rows_per_thread, o.intra_rows);
+    return sw_set_error(SW_ECUDA, "inter-task kernel cannot launch with %d warps (rows %d)",
+                        o.warps_per_block, o.rows_per_thread);
   }
-  p->kc.rows = o.rows_per_thread;
-  p->kc.intra_rows = o.intra_rows;
+  p->kc.variant = o.rows_per_thread;
   p->kc.warps = o.warps_per_block;
   p->kc.blocks = dev_sms * bps;
-  p->kc.smem = search_smem_bytes(o.rows_per_thread, o.intra_rows, o.warps_per_block);
+  p->kc.smem = inter_smem_bytes(o.rows_per_thread, o.warps_per_block);
   const int64_t W = (int64_t)p->kc.blocks * p->kc.warps;
+  // one block of INTRA_WARPS per SM: enough for the int32 items, and the
+  // border scratch (one subject-length row per warp) stays bounded
+  if (intra_blocks_per_sm(o.intra_rows) < 1) {
+    plan_free(p);
+    return sw_set_error(SW_ECUDA, "int32 intra-task kernel cannot launch (rows %d)", o.intra_rows);
+  }
+  p->ikc.variant = o.intra_rows;
+  p->ikc.warps = INTRA_WARPS;
+  p->ikc.blocks = dev_sms;
+  p->ikc.smem = intra_smem_bytes(o.intra_rows);
+  const int64_t WI = (int64_t)p->ikc.blocks * INTRA_WARPS;
   const int pbps = pair_blocks_per_sm();
   if (pbps < 1) {
     plan_free(p);
@@ -518,7 +529,7 @@ extern "C" sw_status sw_plan_create(sw_db* db, int32_t max_queries, int64_t max_
   if (e == cudaSuccess) e = dalloc(&p->params, 1);
   if (e == cudaSuccess) e = dalloc(&p->state, 1);
   if (e == cudaSuccess) e = dalloc(&p->scr.inter_border, (size_t)(W * std::max<int64_t>(p->scr.inter_stride_vec, 1)));
-  if (e == cudaSuccess) e = dalloc(&p->scr.intra_border, (size_t)(W * p->scr.intra_stride));
+  if (e == cudaSuccess) e = dalloc(&p->scr.intra_border, (size_t)(WI * p->scr.intra_stride));
   if (e == cudaSuccess) e = dalloc(&p->scr.flags, (size_t)p->scr.flag_capacity);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&p->params_h, sizeof(SearchParams));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&p->state_h, sizeof(SearchState));
@@ -544,8 +555,10 @@ extern "C" void sw_plan_destroy(sw_plan* plan) {
   plan_free(plan);
 }
 
-// The device work of one search: reset counters, persistent search, recompute.
-// Events around the two kernels give their device time on the launching
+// The device work of one search: reset the counters, then the packed
+// intra-task kernel (long subjects), the inter-task kernel (the rest) and the
+// int32 intra-task kernel (saturated pairs, or everything when the packed path
+// is off).  Events around the kernels give their device time on the launching
 // stream.  Under stream capture an event record only orders the capture
 // unless it carries cudaEventRecordExternal, which makes it a real
 // event-record node of the graph; outside capture that flag is illegal.
@@ -559,9 +572,9 @@ static cudaError_t enqueue_kernels(sw_plan* p, cudaStream_t s, bool capturing) {
   if (e == cudaSuccess) e = record(p->ev[0], s, capturing);
   if (e == cudaSuccess) e = launch_pairs(p->pair_blocks, p->db->view, p->params, p->state, p->scr, s);
   if (e == cudaSuccess) e = record(p->ev[1], s, capturing);
-  if (e == cudaSuccess) e = launch_search(p->kc, 0, p->db->view, p->params, p->state, p->scr, s);
+  if (e == cudaSuccess) e = launch_inter(p->kc, p->db->view, p->params, p->state, p->scr, s);
   if (e == cudaSuccess) e = record(p->ev[2], s, capturing);
-  if (e == cudaSuccess) e = launch_search(p->kc, 1, p->db->view, p->params, p->state, p->scr, s);
+  if (e == cudaSuccess) e = launch_intra(p->ikc, p->db->view, p->params, p->state, p->scr, s);
   if (e == cudaSuccess) e = record(p->ev[3], s, capturing);
   return e;
 }

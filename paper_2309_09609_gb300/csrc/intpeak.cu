@@ -34,7 +34,16 @@ enum IntOp {
   OP_IMAD = 13,        // int32 multiply-add with a run-time multiplier (FMA pipe)
   OP_CELL_BIASED = 14, // the packed cell pair of the search kernel: prmt, vimax3,
                        // viaddmax, imad (H'-Go), viaddmax x2 (6 ops, one on the FMA pipe)
-  OP_COUNT = 15
+  // 8-bit SIMD (four cells per word), for the int8x4 question
+  OP_VADD4 = 15,       // 8x4 wrapping add
+  OP_VMAXU4 = 16,      // 8x4 unsigned max
+  OP_VMAXS4 = 17,      // 8x4 signed max
+  OP_VADDUS4 = 18,     // 8x4 unsigned saturating add
+  OP_VSUBUS4 = 19,     // 8x4 unsigned saturating subtract
+  OP_CELL_U8X4 = 20,   // an unsigned biased 8x4 cell update (four cells): addus, subus,
+                       // maxu x2 (E, F), subus (H - Go), subus x2 (E, F - Ge), maxu x2,
+                       // maxu (S) -- 10 ops
+  OP_COUNT = 21
 };
 
 __host__ __device__ inline int intpeak_ops_per_step(int op) {
@@ -43,6 +52,7 @@ __host__ __device__ inline int intpeak_ops_per_step(int op) {
     case OP_CELL_S16X2_PRMT: return 7;
     case OP_CELL_I32: return 10;
     case OP_CELL_BIASED: return 6;
+    case OP_CELL_U8X4: return 10;
     default: return 1;
   }
 }
@@ -66,6 +76,21 @@ __device__ __forceinline__ void step(uint32_t (&a)[CHAINS], uint32_t c0, uint32_
     else if (OP == OP_VSUB2) r = __vsub2(x, y);
     else if (OP == OP_VADDSS2) r = __vaddss2(x, y);
     else if (OP == OP_PRMT) r = __byte_perm(x, y, 0xC480 + (i & 3) * 0x1111);
+    else if (OP == OP_VADD4) r = __vadd4(x, y);
+    else if (OP == OP_VMAXU4) r = __vmaxu4(x, y);
+    else if (OP == OP_VMAXS4) r = __vmaxs4(x, y);
+    else if (OP == OP_VADDUS4) r = __vaddus4(x, y);
+    else if (OP == OP_VSUBUS4) r = __vsubus4(x, y);
+    else if (OP == OP_CELL_U8X4) {
+      // x: H diag / F, y: biased profile word / E; c0 = Go (x4), c1 = Ge (x4).
+      // Unsigned saturation at 0 gives the zero term of Eq. 1 for free.
+      uint32_t h = __vsubus4(__vaddus4(x, y), c0 ^ c1);  // H = hd + (w + bias) - bias
+      h = __vmaxu4(h, __vmaxu4(x, y));                    // max(., E, F)
+      const uint32_t t = __vsubus4(h, c0);                 // H - Go
+      const uint32_t e = __vmaxu4(__vsubus4(y, c1), t);    // Eq. 2
+      const uint32_t f = __vmaxu4(__vsubus4(x, c1), t);    // Eq. 3
+      r = __vmaxu4(e, f) ^ h;                              // S-like fold
+    }
     else if (OP == OP_IMAD) {
       asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(x), "r"(c1), "r"(y));
     } else if (OP == OP_CELL_BIASED) {
@@ -140,6 +165,12 @@ static IntpeakKernel intpeak_pick(int op) {
     case OP_CELL_I32: return intpeak_kernel<OP_CELL_I32>;
     case OP_IMAD: return intpeak_kernel<OP_IMAD>;
     case OP_CELL_BIASED: return intpeak_kernel<OP_CELL_BIASED>;
+    case OP_VADD4: return intpeak_kernel<OP_VADD4>;
+    case OP_VMAXU4: return intpeak_kernel<OP_VMAXU4>;
+    case OP_VMAXS4: return intpeak_kernel<OP_VMAXS4>;
+    case OP_VADDUS4: return intpeak_kernel<OP_VADDUS4>;
+    case OP_VSUBUS4: return intpeak_kernel<OP_VSUBUS4>;
+    case OP_CELL_U8X4: return intpeak_kernel<OP_CELL_U8X4>;
     default: return nullptr;
   }
 }
@@ -193,7 +224,8 @@ int intpeak_run(int op, int blocks_per_sm, int threads, int iters, double* lane_
 int main() {
   const char* names[] = {"iadd", "imax", "viaddmax_s32", "viaddmax_s16x2", "viaddmax_s16x2_relu",
                          "vimax3_s16x2", "vmaxs2", "vsub2", "vaddss2", "prmt", "cell_s16x2",
-                         "cell_s16x2_prmt", "cell_i32", "imad", "cell_biased"};
+                         "cell_s16x2_prmt", "cell_i32", "imad", "cell_biased", "vadd4", "vmaxu4",
+                         "vmaxs4", "vaddus4", "vsubus4", "cell_u8x4"};
   for (int op = 0; op < swgb::OP_COUNT; op++) {
     for (int bps : {4, 8}) {
       double r, mhz, s;

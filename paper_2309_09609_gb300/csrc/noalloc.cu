@@ -12,7 +12,7 @@
 // array until the process exits.
 //
 // The kernel is a variant of the int32 intra-task warp wavefront of
-// search_kernels.cu: one warp per (query, subject) pair, lane k owning TI
+// intra_kernel.cu: one warp per (query, subject) pair, lane k owning TI
 // query rows of a 32*TI-row pass, (H, F) borders handed to the next lane by
 // __shfl_up_sync, and the border between passes kept in this array.
 #include <mutex>

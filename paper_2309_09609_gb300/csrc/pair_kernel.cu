@@ -1,0 +1,245 @@
+// pair_kernel.cu -- the packed intra-task kernel of libswgb (long subjects).
+#include <type_traits>
+
+#include "device_common.cuh"
+
+namespace swgb {
+
+// ---- packed intra-task kernel: one warp per pair of long subjects ----------
+// The two subjects of a pair are adjacent in length order, packed as the two
+// 16-bit halves of every word (the shorter one reads pad columns past its
+// end, which cannot raise its score).  Lane k owns PR query rows of a
+// 32*PR-row pass, split into PQ quarters of PQR rows; quarter q of lane k
+// updates column t - PQ*k - q at step t (Section II-B, intra-task
+// parallelism with neighbour border exchange):
+//   * quarter q needs the bottom row of quarter q - 1 at the same column
+//     (produced one step earlier) and its H' one column back (two steps
+//     earlier), so the PQ quarter updates of a step are independent;
+//   * quarter 0 receives the bottom row of lane k - 1 (its quarter PQ - 1,
+//     one step earlier) by __shfl_up_sync; lane 0 reads the previous pass's
+//     bottom row from this warp's border scratch and lane 31 writes it (index
+//     c is read at step c and rewritten at step c + 32*PQ - 1).
+// Residues are staged in a per-warp shared-memory ring 128 columns ahead;
+// quarter 0 loads the 16-byte profile row of its column and later quarters
+// reuse its words.  Values carry the +Go bias of the inter-task kernel, and a
+// pair half whose S' reaches the threshold is recomputed in int32 like any
+// other saturated pair.
+constexpr int PR = 16;                          // packed rows per lane
+constexpr int PQ = 4;                           // quarters (independent chains) per lane
+constexpr int PQR = PR / PQ;                    // rows per quarter
+constexpr int PAIR_PROFILE = NCODES * 32 * PR;  // int8 [code][lane][PR]
+constexpr int PRING = 384;                      // residue ring per subject: 3 blocks of 128
+constexpr int PAIR_SLICE = PAIR_PROFILE + 2 * PRING;
+
+__global__ void __launch_bounds__(PAIR_WARPS * 32, 4)
+pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scratch scr) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  int8_t* sm = (int8_t*)smem;
+  load_matrix(sm, P);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  uint8_t* prof = smem + MATRIX_SMEM + wib * PAIR_SLICE;
+  uint8_t* ring0 = prof + PAIR_PROFILE;
+  uint8_t* ring1 = ring0 + PRING;
+  const int64_t warp_id = (int64_t)blockIdx.x * PAIR_WARPS + wib;
+  uint2* hb = scr.pair_border + warp_id * scr.pair_stride;
+  const int nq = P->nq;
+  if (nq <= 0) return;
+  const int64_t total = P->n_pair_items;
+  const int go = P->go;
+  const uint32_t GO2 = pack2(go), NGE2 = pack2(-P->ge);
+  const uint32_t MGO = (uint32_t)(-(int)((uint32_t)go * 65537u));
+  const uint32_t one = (uint32_t)P->one;
+  constexpr int ROWS = 32 * PR;
+  for (;;) {
+    unsigned long long it = 0;
+    if (lane == 0) it = atomicAdd(&st->pair_work, 1ull);
+    it = __shfl_sync(FULL, it, 0);
+    if ((int64_t)it >= total) break;
+    const int pair = (int)((int64_t)it / nq);
+    const int q = P->qorder[(int64_t)it % nq];
+    const int s0 = 2 * pair, s1 = 2 * pair + 1;
+    const bool has1 = s1 < P->n_long;
+    const int n0 = db.clen[s0], n1 = has1 ? db.clen[s1] : 0;  // n0 >= n1 (sorted)
+    const uint8_t* __restrict__ d0 = db.cont + db.coff[s0];
+    const uint8_t* __restrict__ d1 = has1 ? db.cont + db.coff[s1] : d0;
+    const int m = P->qlen[q];
+    const uint8_t* __restrict__ qr = P->qres + P->qoff[q];
+    const int npass = n0 > 0 ? (m + ROWS - 1) / ROWS : 0;
+    // residues of columns [128 b, 128 b + 128) into ring slot b % 3 (pad past the end)
+    auto load_block = [&](int b) {
+      const int c = 128 * b + 4 * lane;
+      uint32_t w0 = 0, w1 = 0;
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        const int cc = c + i;
+        w0 |= (uint32_t)(cc < n0 ? d0[cc] : PAD_CODE) << (8 * i);
+        w1 |= (uint32_t)(cc < n1 ? d1[cc] : PAD_CODE) << (8 * i);
+      }
+      *(uint32_t*)(ring0 + c % PRING) = w0;
+      *(uint32_t*)(ring1 + c % PRING) = w1;
+    };
+    uint32_t smax = GO2;
+    for (int p = 0; p < npass; p++) {
+      __syncwarp();
+      lane_profile<PR>(prof, sm, qr, m, p * ROWS + lane * PR, lane);  // this lane's PR rows
+      load_block(0);
+      __syncwarp();
+      uint32_t Hp[PR], E[PR];
+#pragma unroll
+      for (int r = 0; r < PR; r++) {
+        Hp[r] = GO2;  // H(i, 0) = 0
+        E[r] = 0u;    // E(i, 1) = -Go
+      }
+      // quarter q's bottom-row H' one and two steps back, its F' one step back
+      uint32_t qh1[PQ], qh2[PQ], qf1[PQ];
+#pragma unroll
+      for (int k = 0; k < PQ; k++) {
+        qh1[k] = GO2;
+        qh2[k] = GO2;
+        qf1[k] = 0u;
+      }
+      // profile vectors of the last four steps in slot (t mod 4): quarter q at
+      // step t uses word q of the vector loaded at step t - q; steps run in
+      // blocks of four so every slot index is a compile-time constant
+      uint4 VA[PQ], VB[PQ];
+#pragma unroll
+      for (int k = 0; k < PQ; k++) {
+        VA[k] = make_uint4(0u, 0u, 0u, 0u);
+        VB[k] = make_uint4(0u, 0u, 0u, 0u);
+      }
+      uint32_t hdiag = GO2, out_h = GO2, out_f = 0u;
+      const bool last_pass = (p == npass - 1);
+      const int steps = n0 + 32 * PQ - 1;
+      // ring position of column t0 - PQ*lane; a multiple of 4, as is PRING
+      int pos = (PRING - (PQ * lane) % PRING) % PRING;
+      // one step of the wavefront; CHECK: some quarter may lie outside the
+      // columns (ramp-up and drain); in the steady state every quarter of
+      // every lane is inside, so the step needs no per-quarter test
+      auto step = [&](const int t, auto checked, auto slot) {
+        constexpr bool CHECK = decltype(checked)::value;
+        constexpr int U = decltype(slot)::value;  // t mod 4
+        if constexpr (U == 0) {
+          if ((t & 127) == 0) {
+            load_block((t >> 7) + 1);
+            __syncwarp();
+          }
+        }
+        uint32_t in_h = __shfl_up_sync(FULL, out_h, 1);
+        uint32_t in_f = __shfl_up_sync(FULL, out_f, 1);
+        const int c0 = t - PQ * lane;  // quarter 0's column
+        if (lane == 0) {
+          if (p > 0 && c0 < n0) {
+            const uint2 v = hb[c0];
+            in_h = v.x;
+            in_f = v.y;
+          } else {
+            in_h = GO2;  // H(0, j) = 0
+            in_f = 0u;   // F(1, j) = -Go
+          }
+        }
+        // a ring slot not yet filled (this lane has not started) may hold any
+        // byte: clamp so the profile address stays inside this warp's slice
+        const int ra = min((int)ring0[pos + U], PAD_CODE);
+        const int rb = min((int)ring1[pos + U], PAD_CODE);
+        VA[U] = *(const uint4*)(prof + (ra * 32 + lane) * PR);
+        VB[U] = *(const uint4*)(prof + (rb * 32 + lane) * PR);
+        const uint32_t wa[PQ] = {VA[U].x, VA[(U + 3) & 3].y, VA[(U + 2) & 3].z, VA[(U + 1) & 3].w};
+        const uint32_t wb[PQ] = {VB[U].x, VB[(U + 3) & 3].y, VB[(U + 2) & 3].z, VB[(U + 1) & 3].w};
+        uint32_t nh[PQ], nf[PQ];
+#pragma unroll
+        for (int k = 0; k < PQ; k++) {
+          const int col = c0 - k;
+          bool active = true;
+          if constexpr (CHECK) active = col >= 0 && col < n0;
+          nh[k] = qh1[k];
+          nf[k] = qf1[k];
+          if (active) {
+            uint32_t hd = k == 0 ? hdiag : qh2[k - 1];  // H' one row up, one column back
+            uint32_t f = k == 0 ? in_f : qf1[k - 1];    // F' of this quarter's first row
+            uint32_t hprev = 0;
+#pragma unroll
+            for (int i = 0; i < PQR; i++) {
+              const int r = k * PQR + i;
+              uint32_t e = E[r];
+              const uint32_t h = packed_cell(hd, prmt(wa[k], wb[k], sext_pair_sel(i)), e, f, GO2,
+                                             NGE2, MGO, one);
+              hd = Hp[r];
+              Hp[r] = h;
+              E[r] = e;
+              if (i & 1)
+                smax = __vimax3_s16x2(smax, hprev, h);
+              else
+                hprev = h;
+            }
+            nh[k] = Hp[k * PQR + PQR - 1];
+            nf[k] = f;
+            if (k == PQ - 1 && lane == 31 && !last_pass) hb[col] = make_uint2(nh[k], f);
+          } else if (col < 0) {
+            nh[k] = GO2;  // left of the matrix: H = 0
+          }
+        }
+        hdiag = in_h;
+        out_h = nh[PQ - 1];
+        out_f = nf[PQ - 1];
+#pragma unroll
+        for (int k = 0; k < PQ; k++) {
+          qh2[k] = qh1[k];
+          qh1[k] = nh[k];
+          qf1[k] = nf[k];
+        }
+      };
+      auto block = [&](const int t0, auto checked) {
+        step(t0, checked, std::integral_constant<int, 0>{});
+        step(t0 + 1, checked, std::integral_constant<int, 1>{});
+        step(t0 + 2, checked, std::integral_constant<int, 2>{});
+        step(t0 + 3, checked, std::integral_constant<int, 3>{});
+        pos = pos + 4 == PRING ? 0 : pos + 4;
+      };
+      // every quarter of every lane is inside the columns for 32*PQ-1 <= t < n0;
+      // the last block may run past `steps`, where every quarter is outside
+      int t0 = 0;
+      for (; t0 < 32 * PQ; t0 += 4) block(t0, std::true_type{});
+#pragma unroll 1
+      for (; t0 + 4 <= n0; t0 += 4) block(t0, std::false_type{});
+      for (; t0 < steps; t0 += 4) block(t0, std::true_type{});
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) smax = __vmaxs2(smax, __shfl_xor_sync(FULL, smax, o));
+    if (lane < 2 && (lane == 0 || has1)) {
+      const int sidx = lane ? s1 : s0;
+      const int sb = (int)(int16_t)(lane ? (smax >> 16) : (smax & 0xffffu));  // S'
+      const int orig = db.perm[sidx];
+      if (orig >= 0) {
+        if (sb >= P->sat_threshold) {
+          const unsigned long long k = atomicAdd(&st->n_flags, 1ull);
+          if ((int64_t)k < scr.flag_capacity) scr.flags[k] = make_int2(q, sidx);
+        } else {
+          P->scores[(int64_t)q * db.n + orig] = sb - go;
+        }
+      }
+    }
+  }
+}
+
+size_t pair_smem_bytes() { return (size_t)MATRIX_SMEM + (size_t)PAIR_WARPS * PAIR_SLICE; }
+
+int pair_blocks_per_sm() {
+  const size_t smem = pair_smem_bytes();
+  if (cudaFuncSetAttribute(pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return 0;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_kernel, PAIR_WARPS * 32, smem) !=
+      cudaSuccess)
+    return 0;
+  return nb;
+}
+
+cudaError_t launch_pairs(int blocks, const DbView& db, const SearchParams* params,
+                         SearchState* state, const Scratch& scr, cudaStream_t stream) {
+  pair_kernel<<<blocks, PAIR_WARPS * 32, pair_smem_bytes(), stream>>>(db, params, state, scr);
+  return cudaGetLastError();
+}
+
+}  // namespace swgb

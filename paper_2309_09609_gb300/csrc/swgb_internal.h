@@ -54,7 +54,7 @@ struct SearchParams {
   const int32_t* qlen;    // [nq]
   const int32_t* qorder;  // [nq] query indices, longest first
   int32_t* scores;        // [nq x N] caller order
-  int64_t n_intra_items;  // n_long x nq  (int32 intra-task items, when not packed)
+  int64_t n_intra_items;  // n_long x nq  (int32 intra-task items, when the packed path is off)
   int64_t n_inter_items;  // inter groups x nq  (packed inter-task items)
   int64_t n_pair_items;   // ceil(n_long / 2) x nq  (packed intra-task items: subject pairs)
   int32_t nq;
@@ -69,11 +69,12 @@ struct SearchParams {
 
 // ---- per-search device state (zeroed before each search) --------------------
 struct SearchState {
-  unsigned long long work;       // next work item (search kernel)
-  unsigned long long n_flags;    // saturated pairs appended to the flag list
-  unsigned long long recompute;  // next flag item (recompute kernel)
-  unsigned long long pair_work;  // next work item (packed intra-task kernel)
-  unsigned int status;           // reserved: error bits raised on the device
+  unsigned long long work;        // next work item (inter-task kernel)
+  unsigned long long n_flags;     // saturated pairs appended to the flag list
+  unsigned long long recompute;   // next flagged pair (int32 intra-task kernel, per block)
+  unsigned long long pair_work;   // next work item (packed intra-task kernel)
+  unsigned long long intra_work;  // next int32 intra-task item (per warp)
+  unsigned int status;            // reserved: error bits raised on the device
   unsigned int pad;
 };
 
@@ -89,32 +90,36 @@ struct Scratch {
   int64_t pair_stride;        // uint2 per warp
 };
 
-// ---- kernel launchers (search_kernels.cu) -------------------------------------
+// ---- kernel launchers -----------------------------------------------------------
 struct KernelConfig {
-  int rows;        // packed rows per thread (16 or 32)
-  int intra_rows;  // int32 rows per lane (8 or 16)
+  int variant;     // inter: packed rows per thread (16/32); intra: int32 rows per lane (8/16)
   int warps;       // warps per block
   int blocks;      // grid size
   size_t smem;     // dynamic shared memory per block
 };
 
-// Shared-memory bytes a block needs for a configuration.
-size_t search_smem_bytes(int rows, int intra_rows, int warps);
-// Resident blocks per SM for a configuration (0 if it cannot launch).
-int search_blocks_per_sm(int rows, int intra_rows, int warps);
-// mode 0: search (intra items, then inter items); mode 1: recompute flagged pairs.
-cudaError_t launch_search(const KernelConfig& kc, int mode, const DbView& db,
-                          const SearchParams* params, SearchState* state, const Scratch& scr,
-                          cudaStream_t stream);
+// Inter-task kernel, packed 16-bit (inter_kernel.cu).
+size_t inter_smem_bytes(int rows, int warps);
+int inter_blocks_per_sm(int rows, int warps);  // resident blocks per SM, 0 if it cannot launch
+cudaError_t launch_inter(const KernelConfig& kc, const DbView& db, const SearchParams* params,
+                         SearchState* state, const Scratch& scr, cudaStream_t stream);
 
-// Packed intra-task kernel over subject pairs (long subjects).
+// Int32 intra-task kernel (intra_kernel.cu): int32 items one warp each, then
+// flagged pairs one block each.  Scratch: one border row per warp.
+constexpr int INTRA_WARPS = 16;  // warps per block
+size_t intra_smem_bytes(int rows);
+int intra_blocks_per_sm(int rows);
+cudaError_t launch_intra(const KernelConfig& kc, const DbView& db, const SearchParams* params,
+                         SearchState* state, const Scratch& scr, cudaStream_t stream);
+
+// Packed intra-task kernel over subject pairs, long subjects (pair_kernel.cu).
 constexpr int PAIR_WARPS = 4;  // warps per block
 int pair_blocks_per_sm();
 size_t pair_smem_bytes();
 cudaError_t launch_pairs(int blocks, const DbView& db, const SearchParams* params,
                          SearchState* state, const Scratch& scr, cudaStream_t stream);
 
-// Plain int32 baseline (Algorithm 1 per cell), one query per launch.
+// Plain int32 baseline (Algorithm 1 per cell), one query per launch (plain_kernel.cu).
 int plain_blocks_per_sm();
 cudaError_t launch_plain(int blocks, const DbView& db, const SearchParams* params, int query,
                          int2* border, const int64_t* border_off, cudaStream_t stream);

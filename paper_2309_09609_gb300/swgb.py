@@ -23,7 +23,8 @@ ALPHABET = "ARNDCQEGHILKMFPSTWYVBZX*"
 #: intpeak op codes (sw_intpeak)
 INTPEAK_OPS = ["iadd", "imax", "viaddmax_s32", "viaddmax_s16x2", "viaddmax_s16x2_relu",
                "vimax3_s16x2", "vmaxs2", "vsub2", "vaddss2", "prmt", "cell_s16x2",
-               "cell_s16x2_prmt", "cell_i32", "imad", "cell_biased"]
+               "cell_s16x2_prmt", "cell_i32", "imad", "cell_biased", "vadd4", "vmaxu4",
+               "vmaxs4", "vaddus4", "vsubus4", "cell_u8x4"]
 
 
 class SwError(RuntimeError):

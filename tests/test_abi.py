@@ -75,3 +75,13 @@ def test_null_handles_are_rejected(lib):
     lib.sw_db_destroy(None)
     lib.sw_plan_destroy(None)
     assert lib.sw_db_subjects(None) == 0
+
+
+def test_intpeak_rejects_bad_arguments_before_touching_the_gpu(lib):
+    out = np.zeros(3, dtype=np.float64)
+    p = out.ctypes.data_as(ctypes.c_void_p)
+    assert lib.sw_intpeak(len(swgb.INTPEAK_OPS), 8, 256, 100, p) == swgb.SW_EINVAL
+    assert lib.sw_intpeak(-1, 8, 256, 100, p) == swgb.SW_EINVAL
+    assert lib.sw_intpeak(0, 0, 256, 100, p) == swgb.SW_EINVAL
+    assert lib.sw_intpeak(0, 8, 2048, 100, p) == swgb.SW_EINVAL
+    assert lib.sw_intpeak(0, 8, 256, 100, None) == swgb.SW_EINVAL

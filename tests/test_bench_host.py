@@ -17,8 +17,13 @@ def _args(**kw):
 
 
 def test_traffic_record_applies_only_to_the_profiled_kernel_and_workload():
+    rec = bench.traffic_record()
+    same = rec.get("kernel_sources_sha256") == bench.kernel_sources_sha256()
     t = bench.profiled_traffic(_args())
-    assert isinstance(t, int) and t > 1e11          # recorded for the current kernel source
+    if same:                                        # recorded for the current kernel sources
+        assert isinstance(t, int) and t == int(rec["dram_bytes_per_launch"]) and t > 1e11
+    else:                                           # kernel changed since the capture
+        assert t is None
     assert bench.profiled_traffic(_args(subjects=1000)) is None
     assert bench.profiled_traffic(_args(rows=16)) is None
     assert bench.profiled_traffic(_args(cutoff=3000)) is None
@@ -31,3 +36,16 @@ def test_workload_query_subset():
     w2 = bench.make_workload("paper-search", 0, subjects=2000, queries=3, query_offset=5)
     assert len(w2.db) == 2000 and len(w2.queries) == 3
     assert w2.queries.lens[0] == bench.make_workload("paper-search", 0, subjects=2000).queries.lens[5]
+
+
+def test_oracle_sample_fits_the_cell_budget():
+    for name in ("plain-small", "paper-search"):
+        w = bench.make_workload(name, 0, subjects=5000 if name == "paper-search" else None)
+        for budget in (1e6, 1e8, 1e9):
+            sub = bench.oracle_sample(w, budget)
+            cells = int(w.queries.total) * int(sub.total)
+            assert len(sub) >= 1
+            assert cells <= budget or len(sub) == 1
+            if len(sub) < len(w.db):          # one more subject would not fit
+                assert cells + int(w.queries.total) * int(w.db.lens[len(sub)]) > budget
+            assert (sub.lens == w.db.lens[:len(sub)]).all()

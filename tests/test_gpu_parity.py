@@ -144,6 +144,28 @@ def test_saturation_with_large_matrix_entries():
     assert_exact(res, want)
 
 
+@pytest.mark.parametrize("intra_rows", [8, 16])
+def test_recompute_spans_several_rounds_of_passes(intra_rows):
+    # A flagged pair is recomputed by one block whose 16 warps take the query's
+    # 32*TI-row passes in turn.  A 9,000-residue query has 36 (TI = 8) or 18
+    # (TI = 16) passes, more than one round of warps.  The flagged subjects are
+    # shorter (400: a pass lasts fewer stages than the 48 between a warp's
+    # pass starts) and longer (2,000; 5,000) than that.
+    rng = np.random.default_rng(70 + intra_rows)
+    m = rand_matrix(rng, -20, 10)
+    np.fill_diagonal(m, 100)
+    q = seqset(rng, [9000, 700])
+    q0 = q.seq(0)
+    pieces = [q0[100:500], q0[3000:5000], q0[4000:9000], q0[8600:9000][::-1].copy()]
+    flagged = synth.SeqSet(np.concatenate(pieces), np.array([p.size for p in pieces], np.int32))
+    db = concat(flagged, seqset(rng, rng.integers(5, 600, size=70)))
+    want = oracle_all(q, db, 10, 2, m.astype(np.int32))
+    assert (want > 32767).sum() >= 3
+    res, st = all_paths(q, db, 10, 2, m, intra_rows=intra_rows)
+    assert st["recomputed_pairs"] >= 3
+    assert_exact(res, want)
+
+
 def test_huge_gap_penalties_take_the_int32_path():
     rng = np.random.default_rng(8)
     db = seqset(rng, rng.integers(0, 120, size=90))
