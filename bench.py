@@ -75,6 +75,9 @@ def parse():
     ap.add_argument("--serve", type=int, default=200,
                     help="serving leg: arrivals replayed against the resident DB (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=50.0, help="Poisson arrival rate (1/s)")
+    ap.add_argument("--serve-slots", type=int, default=4,
+                    help="concurrent batches (plans with their own stream) in the serving leg")
+    ap.add_argument("--serve-batch", type=int, default=16, help="largest batch of the serving leg")
     ap.add_argument("--tune", action="store_true",
                     help="pick the tile shape with the autotuner before timing")
     ap.add_argument("--no-plain", action="store_true")
@@ -266,7 +269,8 @@ def run_serving(d, db, args, opts, w):
     resident database through the continuous-batching server."""
     from paper_2309_09609_gb300 import serve, synth
     trace = synth.serving_trace(seed=args.seed, n=args.serve, rate=args.serve_rate)
-    srv = serve.Server(d, slots=4, max_batch=16, max_batch_residues=65536,
+    srv = serve.Server(d, slots=args.serve_slots, max_batch=args.serve_batch,
+                       max_batch_residues=max(65536, 4096 * args.serve_batch),
                        gap_open=w.gap_open, gap_extend=w.gap_extend, **opts)
     t0 = time.perf_counter()
     try:
@@ -284,7 +288,8 @@ def run_serving(d, db, args, opts, w):
             "p50_ms": round(rep["p50_ms"], 2), "p99_ms": round(rep["p99_ms"], 2),
             "gcups": round(rep["gcups"], 1), "offered_gcups": round(offered, 1),
             "batches": rep["batches"], "mean_batch": round(rep["mean_batch"], 2),
-            "max_concurrent_batches": rep["max_concurrent_batches"], "slots": 4,
+            "max_concurrent_batches": rep["max_concurrent_batches"], "slots": args.serve_slots,
+            "max_batch": args.serve_batch,
             "wall_s": round(wall, 2), "alone_equals_mixed": bool(same)}
 
 
