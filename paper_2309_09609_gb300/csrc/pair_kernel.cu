@@ -41,6 +41,11 @@ pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scra
   uint8_t* prof = smem + MATRIX_SMEM + wib * PAIR_SLICE;
   uint8_t* ring0 = prof + PAIR_PROFILE;
   uint8_t* ring1 = ring0 + PRING;
+  // Every ring byte holds a residue code (<= PAD_CODE) from here on: slots a
+  // lane reads before its first column (the ramp of each pass) then still
+  // address a row inside this warp's profile.
+  for (int i = lane; i < 2 * PRING; i += 32) ring0[i] = PAD_CODE;
+  __syncwarp();
   const int64_t warp_id = (int64_t)blockIdx.x * PAIR_WARPS + wib;
   uint2* hb = scr.pair_border + warp_id * scr.pair_stride;
   const int nq = P->nq;
@@ -138,10 +143,8 @@ pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scra
             in_f = 0u;   // F(1, j) = -Go
           }
         }
-        // a ring slot not yet filled (this lane has not started) may hold any
-        // byte: clamp so the profile address stays inside this warp's slice
-        const int ra = min((int)ring0[pos + U], PAD_CODE);
-        const int rb = min((int)ring1[pos + U], PAD_CODE);
+        const int ra = ring0[pos + U];
+        const int rb = ring1[pos + U];
         VA[U] = *(const uint4*)(prof + (ra * 32 + lane) * PR);
         VB[U] = *(const uint4*)(prof + (rb * 32 + lane) * PR);
         const uint32_t wa[PQ] = {VA[U].x, VA[(U + 3) & 3].y, VA[(U + 2) & 3].z, VA[(U + 1) & 3].w};
