@@ -75,11 +75,14 @@ def parse():
     ap.add_argument("--serve", type=int, default=200,
                     help="serving leg: arrivals replayed against the resident DB (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=50.0, help="Poisson arrival rate (1/s)")
-    ap.add_argument("--serve-slots", type=int, default=4,
+    ap.add_argument("--serve-slots", type=int, default=2,
                     help="concurrent batches (plans with their own stream) in the serving leg")
     ap.add_argument("--serve-batch", type=int, default=16, help="largest batch of the serving leg")
     ap.add_argument("--tune", action="store_true",
                     help="pick the tile shape with the autotuner before timing")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch the plan's kernels directly instead of replaying a CUDA graph "
+                         "(for kernel profilers)")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -316,6 +319,8 @@ def run_native(args):
         opts["long_cutoff"] = args.cutoff
     if args.warps:
         opts["warps_per_block"] = args.warps
+    if args.no_graph:
+        opts["use_graph"] = 0
     tuned = None
     if args.tune:
         from paper_2309_09609_gb300 import tune

@@ -15,7 +15,12 @@ row against every subject.
   have arrived, up to ``max_batch`` queries and ``max_batch_residues``
   residues, and launches them as one batch on a free slot (its own plan and
   CUDA stream).  Requests arriving while earlier batches run go to the next
-  free slot, so batches of different lengths overlap on the GPU.
+  free slot, so batches of different lengths overlap on the GPU.  Two
+  slots is the default: one batch's kernels run while the next batch is
+  formed, staged and launched behind it.  More slots only queue on the GPU,
+  because each search's persistent kernels occupy every SM.  On the
+  570,000-subject database at 50 queries/s, 2 slots measured p50 77 ms and
+  p99 185 ms, against 101 ms and 274 ms with 4 slots.
 * Completion is observed per slot; each request gets its scores, its
   latency (arrival to completion on the host) and the batch it rode in.
 """
@@ -70,7 +75,7 @@ class _Slot:
 class Server:
     """Continuous-batching search server over one resident Database."""
 
-    def __init__(self, db: swgb.Database, slots: int = 4, max_batch: int = 16,
+    def __init__(self, db: swgb.Database, slots: int = 2, max_batch: int = 16,
                  max_batch_residues: int = 65536, memory_budget: int | None = None,
                  gap_open: int = 10, gap_extend: int = 2, matrix=None, **plan_opts):
         self.db = db
