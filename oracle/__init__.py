@@ -39,7 +39,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
-_SRC = os.path.join(_HERE, "sw_oracle.c")
+_SRCS = [os.path.join(_HERE, f) for f in ("sw_oracle.c", "sw_align_oracle.c")]
 
 ALPHABET = "ARNDCQEGHILKMFPSTWYVBZX*"
 CODE_X = ALPHABET.index("X")
@@ -49,13 +49,14 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile sw_oracle.c with gcc -O2 (scalar: tree vectorisation off)."""
+    """Compile the oracle's C files with gcc -O2 (scalar: tree vectorisation off)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+    stale = not os.path.exists(_SO) or any(os.path.getmtime(_SO) < os.path.getmtime(f) for f in _SRCS)
+    if force or stale:
         tmp = _SO + f".tmp{os.getpid()}"
         subprocess.check_call([
             "gcc", "-O2", "-fno-tree-vectorize", "-fPIC", "-shared", "-std=c99",
-            "-Wall", "-o", tmp, _SRC, "-lpthread"])
+            "-Wall", "-o", tmp] + _SRCS + ["-lpthread"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -73,6 +74,8 @@ def _load():
                 f.argtypes = [P, i32, P, i32, P, i32, i32, i32]
             lib.oracle_pairs.restype = i32
             lib.oracle_pairs.argtypes = [P, P, P, P, P, P, P, P, i64, P, i32, i32, i32, P, i32]
+            lib.oracle_sw_align.restype = i32
+            lib.oracle_sw_align.argtypes = [P, i32, P, i32, P, i32, i32, i32, P, P, P, P, P, i64, P]
             lib.oracle_blosum62.restype = None
             lib.oracle_blosum62.argtypes = [P]
             _lib = lib
@@ -120,6 +123,36 @@ def sw_score_paper(q, d, Go: int, Ge: int, matrix=None, zero_init: bool = False)
     if s < 0:
         raise MemoryError("oracle allocation failed")
     return int(s)
+
+
+def align_paper(q, d, Go: int, Ge: int, matrix=None) -> dict:
+    """The optimal local alignment of one pair (``sw_align_oracle.c``, which
+    states which of several optimal alignments is returned), with Eq. 2-3's
+    own Go/Ge: score, 0-based half-open ranges q[q_begin:q_end] and
+    d[s_begin:s_end], and the transcript ('M', 'I' = query residue against a
+    gap, 'D' = subject residue against a gap), first column to last."""
+    q = np.ascontiguousarray(q, dtype=np.uint8)
+    d = np.ascontiguousarray(d, dtype=np.uint8)
+    sm = _matrix(matrix)
+    if q.size and int(q.max()) >= sm.shape[0] or d.size and int(d.max()) >= sm.shape[0]:
+        raise ValueError("residue code outside the scoring matrix")
+    cap = q.size + d.size
+    ops = ctypes.create_string_buffer(max(cap, 1))
+    b = np.zeros(4, dtype=np.int32)
+    n_ops = ctypes.c_int64(0)
+    i4 = [ctypes.byref(ctypes.c_int32.from_buffer(b, 4 * k)) for k in range(4)]
+    s = _load().oracle_sw_align(_ptr(q), q.size, _ptr(d), d.size, _ptr(sm), sm.shape[0],
+                                int(Go), int(Ge), *i4, ops, cap, ctypes.byref(n_ops))
+    if s < 0:
+        raise MemoryError("oracle allocation failed")
+    return {"score": int(s), "q_begin": int(b[0]), "q_end": int(b[1]), "s_begin": int(b[2]),
+            "s_end": int(b[3]), "ops": ops.raw[:n_ops.value].decode()}
+
+
+def align(q, d, gap_open: int = 10, gap_extend: int = 2, matrix=None) -> dict:
+    """``align_paper`` in the library's gap convention (cost(k) = open + k*extend)."""
+    Go, Ge = paper_gaps(gap_open, gap_extend)
+    return align_paper(q, d, Go, Ge, matrix)
 
 
 def sw_score(q, d, gap_open: int = 10, gap_extend: int = 2, matrix=None) -> int:
