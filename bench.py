@@ -62,6 +62,10 @@ def parse():
     ap.add_argument("--rows", type=int, default=None, help="packed rows per thread (16/32)")
     ap.add_argument("--cutoff", type=int, default=None, help="inter/intra length cutoff")
     ap.add_argument("--warps", type=int, default=None)
+    ap.add_argument("--wide-min", type=int, default=None,
+                    help="shortest query scored 32 rows per lane against long subjects")
+    ap.add_argument("--wide-min-subject", type=int, default=None,
+                    help="shortest subject pair scored 32 rows per lane")
     ap.add_argument("--cpu-cells", type=float, default=None,
                     help="cell budget of the CPU oracle baseline's sample (all queries x the "
                          "first subjects that fit); default per workload, 10-30 s on 16 cores")
@@ -84,6 +88,7 @@ def parse():
                     help="launch the plan's kernels directly instead of replaying a CUDA graph "
                          "(for kernel profilers)")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-align", action="store_true", help="skip the traceback leg")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
 
@@ -229,25 +234,34 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "inter_kernel_paper-search_traffic.txt")
-# the inter-task kernel's own sources: its file and the device helpers it includes
-KERNEL_SOURCES = [os.path.join(ROOT, "paper_2309_09609_gb300", "csrc", f)
-                  for f in ("inter_kernel.cu", "device_common.cuh")]
+CSRC = os.path.join(ROOT, "paper_2309_09609_gb300", "csrc")
+# ncu DRAM records of a dominant kernel on a benchmark workload, each valid
+# while the kernel's own sources hash to the recorded value:
+# (kernel, workload) -> (record file, sources hashed in order)
+TRAFFIC_RECORDS = {
+    ("inter_kernel", "paper-search"): ("inter_kernel_paper-search_traffic.txt",
+                                       ("inter_kernel.cu", "device_common.cuh")),
+    ("pair_kernel", "long"): ("pair_kernel_long-sequences_traffic.txt",
+                              ("pair_kernel.cu", "device_common.cuh")),
+}
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", TRAFFIC_RECORDS[("inter_kernel", "paper-search")][0])
+KERNEL_SOURCES = [os.path.join(CSRC, f) for f in TRAFFIC_RECORDS[("inter_kernel", "paper-search")][1]]
 
 
-def kernel_sources_sha256():
+def kernel_sources_sha256(sources=None):
     import hashlib
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in sources or KERNEL_SOURCES:
         with open(f, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
 
-def traffic_record():
+def traffic_record(path=None):
     rec = {}
-    if os.path.exists(TRAFFIC_FILE):
-        with open(TRAFFIC_FILE) as fh:
+    path = path or TRAFFIC_FILE
+    if os.path.exists(path):
+        with open(path) as fh:
             for line in fh:
                 if ":" in line and not line.startswith("#"):
                     k, v = line.split(":", 1)
@@ -255,14 +269,21 @@ def traffic_record():
     return rec
 
 
-def profiled_traffic(args):
-    """DRAM bytes per launch of the inter-task kernel from the committed ncu
-    record, if it covers this workload and the kernel's sources are unchanged."""
-    default = (args.workload == "paper-search" and not args.subjects and not args.queries
-               and args.rows in (None, 32) and args.warps in (None, 8)
-               and args.cutoff in (None, 1500) and not args.tune)
-    rec = traffic_record()
-    if not default or rec.get("kernel_sources_sha256") != kernel_sources_sha256():
+def profiled_traffic(args, kernel="inter_kernel"):
+    """DRAM bytes per launch of the dominant kernel from its committed ncu
+    record, if the record covers this workload at its default size and plan,
+    and the kernel's sources are unchanged since the capture."""
+    key = (kernel, args.workload)
+    if key not in TRAFFIC_RECORDS:
+        return None
+    default = (not args.subjects and not args.queries and args.rows in (None, 32)
+               and args.warps in (None, 8) and args.cutoff in (None, 1500) and not args.tune
+               and getattr(args, "wide_min", None) is None
+               and getattr(args, "wide_min_subject", None) is None)
+    fname, srcs = TRAFFIC_RECORDS[key]
+    rec = traffic_record(os.path.join(ROOT, "profiles", fname))
+    sha = kernel_sources_sha256([os.path.join(CSRC, f) for f in srcs])
+    if not default or rec.get("kernel_sources_sha256") != sha:
         return None
     return int(rec["dram_bytes_per_launch"])
 
@@ -296,6 +317,28 @@ def run_serving(d, db, args, opts, w):
             "wall_s": round(wall, 2), "alone_equals_mixed": bool(same)}
 
 
+def run_align(d, q, db, scores, w):
+    """Optimal alignments (with traceback) of every query's best-scoring
+    subject; the call is timed with the host clock around sw_align, which is
+    synchronous and includes its allocations and copies."""
+    import oracle
+    best = scores.argmax(dim=1).cpu().numpy() if hasattr(scores, "argmax") else scores.argmax(1)
+    pq = np.arange(len(q), dtype=np.int32)
+    ps = best.astype(np.int64)
+    d.align(q.res, q.lens, pq[:1], ps[:1], w.gap_open, w.gap_extend)      # warm-up
+    t0 = time.perf_counter()
+    got = d.align(q.res, q.lens, pq, ps, w.gap_open, w.gap_extend)
+    ms = 1e3 * (time.perf_counter() - t0)
+    cells = int(sum(int(q.lens[a]) * int(db.lens[b]) for a, b in zip(pq, ps)))
+    oracle.build()
+    same = all(got[k] == oracle.align(q.seq(int(a)), db.seq(int(b)), w.gap_open, w.gap_extend)
+               for k, (a, b) in enumerate(zip(pq, ps)))
+    return {"pairs": int(pq.size), "cells": cells, "ms": round(ms, 3),
+            "gcups": round(cells / (ms / 1e3) / 1e9, 2),
+            "transcript_columns": int(sum(len(g["ops"]) for g in got)),
+            "equals_oracle": bool(same)}
+
+
 def run_native(args):
     import torch
     rank, world, local, dist = dist_setup(args)
@@ -321,6 +364,10 @@ def run_native(args):
         opts["warps_per_block"] = args.warps
     if args.no_graph:
         opts["use_graph"] = 0
+    if args.wide_min is not None:
+        opts["wide_min_len"] = args.wide_min
+    if args.wide_min_subject is not None:
+        opts["wide_min_subject"] = args.wide_min_subject
     tuned = None
     if args.tune:
         from paper_2309_09609_gb300 import tune
@@ -411,7 +458,7 @@ def run_native(args):
     inter = dominant.startswith("inter_kernel")
     result["roofline"] = {"bound": "alu", "achieved": dom["achieved"], "peak": round(peak, 3),
                           "unit": "Tops/s", "frac": dom["frac"],
-                          "traffic": profiled_traffic(args) if inter else None,
+                          "traffic": profiled_traffic(args, "inter_kernel" if inter else "pair_kernel"),
                           "kernel": dominant, "kernel_ms": dom["ms"], "kernel_cells": dom["cells"],
                           "kernels": per_kernel,
                           "alu_ops_per_cell": PACKED_ALU_OPS_PER_CELL,
@@ -453,6 +500,10 @@ def run_native(args):
     result["e2e"] = {"value": round(world * cells / e2e_s / 1e9, 2), "unit": "GCUPS",
                      "h2d_bytes_per_step": int(q.total + 4 * nq),
                      "d2h_bytes_per_step": int(4 * nq * N), "ms_per_step": round(1e3 * e2e_s, 3)}
+
+    # traceback of each query's best hit (sw_align), checked against the oracle
+    if rank == 0 and world == 1 and args.workload in ("paper-search", "plain-small") and not args.no_align:
+        result["align"] = run_align(d, q, db, out, w)
 
     # serving: the same resident DB, Poisson arrivals, continuous batching
     if args.serve > 0 and args.workload == "paper-search" and rank == 0 and world == 1:

@@ -101,6 +101,13 @@ typedef struct {
                                 kernel every group whose (query, group) work item would
                                 exceed a quarter of one warp's share of the search (load
                                 balance for few long queries); default 0 */
+  int32_t wide_min_len;      /* long subjects are scored 32 query rows per lane (1024-row
+                                passes, fewer instructions per cell, half the warps) instead
+                                of 16 (512-row passes) for queries of at least this many
+                                residues whose padded cost is lower that way ... default 0 */
+  int32_t wide_min_subject;  /* ... against subject pairs whose longer subject has at least
+                                this many residues, or against every pair when the search
+                                has fewer (pair, query) items than 16-row warps; default 4096 */
 } sw_options;
 
 void sw_options_default(sw_options* opt);
@@ -182,6 +189,43 @@ sw_status sw_search(sw_db* db, const uint8_t* queries, const int32_t* q_lengths,
 sw_status sw_search_plain(sw_db* db, const uint8_t* queries, const int32_t* q_lengths,
                           int32_t n_queries, int32_t gap_open, int32_t gap_extend,
                           const int8_t* matrix, int32_t* scores, void* stream);
+
+/* One optimal local alignment (sw_align). */
+typedef struct {
+  int32_t score;             /* S, as sw_search returns it */
+  int32_t q_begin, q_end;    /* aligned query residues [q_begin, q_end), 0-based */
+  int32_t s_begin, s_end;    /* aligned subject residues [s_begin, s_end), 0-based */
+  int32_t n_ops;             /* transcript length; 0 when score is 0 */
+  int64_t ops_offset;        /* the transcript is ops[ops_offset, ops_offset + n_ops) */
+} sw_alignment;
+
+/* Optimal local alignments, with traceback, of selected (query, subject)
+ * pairs: the alignment behind each score, recovered by the traceback of
+ * Section II-B (the score kernels keep only S).  For pair k, query
+ * pair_query[k] (an index into queries / q_lengths) against database
+ * subject pair_subject[k] (caller order).
+ * Which of several optimal alignments is returned: the one ending at the
+ * first cell in row-major order (query position, then subject position)
+ * whose H equals S; walking back, the diagonal term is preferred to E, and E
+ * to F, when they tie, and a gap opens from H when that reaches the gap's
+ * value.  Transcript, first column to last: 'M' (a query and a subject
+ * residue), 'I' (a query residue against a gap), 'D' (a subject residue
+ * against a gap).
+ *   queries, q_lengths: as sw_search (host or device).
+ *   pair_query, pair_subject: n_pairs entries each, host memory.
+ *   out: n_pairs records, host memory.
+ *   ops: host buffer of ops_capacity bytes; pair k's transcript lies in its
+ *        own slot of q_len + s_len bytes (slots back to back in pair order),
+ *        at its end.  Needs ops_capacity >= sum over pairs of q_len + s_len.
+ * Device memory for the direction bits (4 bits per cell of every pair) is
+ * allocated by the call and freed before it returns; pairs are processed in
+ * chunks of at most 8 GiB of bits.  Synchronous on the stream.
+ * Errors: SW_EINVAL (index out of range, short ops buffer, bad gaps or
+ * codes), SW_ENOMEM, SW_ECUDA. */
+sw_status sw_align(sw_db* db, const uint8_t* queries, const int32_t* q_lengths, int32_t n_queries,
+                   const int32_t* pair_query, const int64_t* pair_subject, int32_t n_pairs,
+                   int32_t gap_open, int32_t gap_extend, const int8_t* matrix, sw_alignment* out,
+                   uint8_t* ops, int64_t ops_capacity, void* stream);
 
 /* Exact scores of every (query, subject) pair without allocating any memory.
  * The paper has no counterpart: this entry point serves callers that cannot

@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libswgb.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["api.cu", "inter_kernel.cu", "pair_kernel.cu", "intra_kernel.cu", "plain_kernel.cu",
-           "intpeak.cu", "noalloc.cu"]
+           "align_kernel.cu", "intpeak.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -6,9 +6,11 @@
 //     short (inter-task) and long (intra-task) part follows Section III-A.
 //   * sw_plan_*: a reusable search context.  All device memory is allocated
 //     once; per search only the query block and a parameter block are copied,
-//     and the kernel sequence (reset counters, persistent search, int32
-//     recompute of saturated pairs) is replayed from one CUDA graph.
+//     and the kernel sequence (reset counters; the two pair-kernel widths on
+//     two streams; the inter-task kernel; the int32 kernel for saturated
+//     pairs) is replayed from one CUDA graph.
 //   * sw_search_plain: the int32 baseline, one kernel launch per query.
+//   * sw_align: optimal alignments with traceback of selected pairs.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -106,6 +108,8 @@ extern "C" void sw_options_default(sw_options* opt) {
   opt->use_graph = 1;
   opt->force_int32 = 0;
   opt->auto_cutoff = 0;
+  opt->wide_min_len = 0;
+  opt->wide_min_subject = 4096;
 }
 
 // ---- small helpers ----------------------------------------------------------------
@@ -159,6 +163,7 @@ struct sw_db {
   std::vector<int32_t> glen_h;   // padded group lengths (host copy)
   std::vector<int32_t> clen_h;   // sorted lengths (host copy)
   std::vector<int64_t> cres_h;   // [N + 1] residues of sorted subjects [0, s)
+  std::vector<int32_t> sorted_of_h;  // caller index -> sorted index
   int64_t residues = 0;
   // owned device buffers
   uint8_t* inter = nullptr;
@@ -284,6 +289,8 @@ extern "C" sw_status sw_db_create(const uint8_t* residues, const int32_t* length
   db->cres_h.assign((size_t)N + 1, 0);
   for (int64_t s = 0; s < N; s++) db->cres_h[s + 1] = db->cres_h[s] + clen[s];
   db->clen_h = std::move(clen);
+  db->sorted_of_h.resize((size_t)N);
+  for (int64_t s2 = 0; s2 < N; s2++) db->sorted_of_h[order[s2]] = (int32_t)s2;
   *out = db;
   return SW_OK;
 }
@@ -389,7 +396,8 @@ struct sw_plan {
   int32_t max_queries = 0;
   int64_t max_residues = 0;
   int32_t g_first = 0;      // first inter-task group under the cutoff
-  int32_t pair_blocks = 0;  // grid of the packed intra-task kernel
+  int32_t pair_blocks16 = 0;  // grid of pair_kernel<16>
+  int32_t pair_blocks32 = 0;  // grid of pair_kernel<32>
   // device buffers
   uint8_t* qres = nullptr;
   int64_t* qoff = nullptr;
@@ -411,6 +419,10 @@ struct sw_plan {
   cudaEvent_t done = nullptr;
   // before the pair kernel, before and after the inter-task kernel, after recompute
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // the two pair-kernel widths run on two streams: fork after the reset, join
+  // before the inter-task kernel
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
   bool in_flight = false;
   sw_stats stats{};
   sw_stats pending{};
@@ -425,6 +437,9 @@ static void plan_free(sw_plan* p) {
   if (p->done) cudaEventDestroy(p->done);
   for (auto& e : p->ev)
     if (e) cudaEventDestroy(e);
+  if (p->fork) cudaEventDestroy(p->fork);
+  if (p->join) cudaEventDestroy(p->join);
+  if (p->side) cudaStreamDestroy(p->side);
   cudaFree(p->qres);
   cudaFree(p->qoff);
   cudaFree(p->qlen);
@@ -464,6 +479,8 @@ extern "C" sw_status sw_plan_create(sw_db* db, int32_t max_queries, int64_t max_
   if (o.warps_per_block < 1 || o.warps_per_block > 8)
     return sw_set_error(SW_EINVAL, "warps_per_block must be 1..8");
   if (o.long_cutoff < 0) return sw_set_error(SW_EINVAL, "long_cutoff < 0");
+  if (o.wide_min_len < 0 || o.wide_min_subject < 0)
+    return sw_set_error(SW_EINVAL, "wide_min_len and wide_min_subject must be >= 0");
   CUDA_TRY(cudaSetDevice(db->device));
 
   sw_plan* p = new sw_plan();
@@ -506,13 +523,16 @@ extern "C" sw_status sw_plan_create(sw_db* db, int32_t max_queries, int64_t max_
   p->ikc.blocks = dev_sms;
   p->ikc.smem = intra_smem_bytes(o.intra_rows);
   const int64_t WI = (int64_t)p->ikc.blocks * INTRA_WARPS;
-  const int pbps = pair_blocks_per_sm();
-  if (pbps < 1) {
+  const int pbps16 = pair_blocks_per_sm(16), pbps32 = pair_blocks_per_sm(32);
+  if (pbps16 < 1 || pbps32 < 1) {
     plan_free(p);
     return sw_set_error(SW_ECUDA, "packed intra-task kernel cannot launch");
   }
-  p->pair_blocks = dev_sms * pbps;
-  const int64_t WP = (int64_t)p->pair_blocks * PAIR_WARPS;
+  p->pair_blocks16 = dev_sms * pbps16;
+  p->pair_blocks32 = dev_sms * pbps32;
+  // the two widths may run at the same time, each on its own scratch rows
+  const int64_t WP = (int64_t)(p->pair_blocks16 + p->pair_blocks32) * PAIR_WARPS;
+  p->scr.pair_rows16 = (int64_t)p->pair_blocks16 * PAIR_WARPS;
 
   cudaError_t e = cudaSuccess;
   const int64_t nres = std::max<int64_t>(max_query_residues, 1);
@@ -524,7 +544,7 @@ extern "C" sw_status sw_plan_create(sw_db* db, int32_t max_queries, int64_t max_
   if (e == cudaSuccess) e = dalloc(&p->qres, nres);
   if (e == cudaSuccess) e = dalloc(&p->qoff, max_queries);
   if (e == cudaSuccess) e = dalloc(&p->qlen, max_queries);
-  if (e == cudaSuccess) e = dalloc(&p->qorder, max_queries);
+  if (e == cudaSuccess) e = dalloc(&p->qorder, 2 * (size_t)max_queries);  // qorder, then qpair
   if (e == cudaSuccess) e = dalloc(&p->scores_dev, (size_t)max_queries * std::max<int64_t>(v.n, 1));
   if (e == cudaSuccess) e = dalloc(&p->params, 1);
   if (e == cudaSuccess) e = dalloc(&p->state, 1);
@@ -536,10 +556,13 @@ extern "C" sw_status sw_plan_create(sw_db* db, int32_t max_queries, int64_t max_
   if (e == cudaSuccess) e = cudaMallocHost((void**)&p->qres_h, nres);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&p->qoff_h, sizeof(int64_t) * max_queries);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&p->qlen_h, sizeof(int32_t) * max_queries);
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&p->qorder_h, sizeof(int32_t) * max_queries);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&p->qorder_h, sizeof(int32_t) * 2 * max_queries);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming);
   for (auto& ev : p->ev)
     if (e == cudaSuccess) e = cudaEventCreate(&ev);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     sw_status st = sw_set_cuda_error(e, "sw_plan_create: allocation");
     plan_free(p);
@@ -570,7 +593,15 @@ static cudaError_t record(cudaEvent_t ev, cudaStream_t s, bool capturing) {
 static cudaError_t enqueue_kernels(sw_plan* p, cudaStream_t s, bool capturing) {
   cudaError_t e = cudaMemsetAsync(p->state, 0, sizeof(SearchState), s);
   if (e == cudaSuccess) e = record(p->ev[0], s, capturing);
-  if (e == cudaSuccess) e = launch_pairs(p->pair_blocks, p->db->view, p->params, p->state, p->scr, s);
+  // pair_kernel<32> on the side stream, pair_kernel<16> on this one: the two
+  // persistent grids share the SMs as their blocks come and go, so their
+  // tails overlap.  Under capture the fork and join become graph edges.
+  if (e == cudaSuccess) e = cudaEventRecord(p->fork, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(p->side, p->fork, 0);
+  if (e == cudaSuccess) e = launch_pairs(32, p->pair_blocks32, p->db->view, p->params, p->state, p->scr, p->side);
+  if (e == cudaSuccess) e = launch_pairs(16, p->pair_blocks16, p->db->view, p->params, p->state, p->scr, s);
+  if (e == cudaSuccess) e = cudaEventRecord(p->join, p->side);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->join, 0);
   if (e == cudaSuccess) e = record(p->ev[1], s, capturing);
   if (e == cudaSuccess) e = launch_inter(p->kc, p->db->view, p->params, p->state, p->scr, s);
   if (e == cudaSuccess) e = record(p->ev[2], s, capturing);
@@ -643,7 +674,33 @@ static sw_status plan_enqueue(sw_plan* p, const HostBatch& hb, int32_t nq, int32
   P.n_long = (int32_t)n_long;
   P.g_first = gf;
   P.n_intra_items = packed ? 0 : n_long * nq;
-  P.n_pair_items = packed ? (n_long + 1) / 2 * nq : 0;
+  // the pair kernels' queries: those for pair_kernel<32>, then those for
+  // pair_kernel<16>, each longest first (none when the packed path is off)
+  int32_t* qpair_h = p->qorder_h + nq;
+  int32_t n32 = 0, n16 = 0;
+  auto wide = [&](int32_t m) { return m >= p->opt.wide_min_len && pair_wide(m); };
+  // subject pairs eligible for the wide kernel: those whose longer subject
+  // has at least wide_min_subject residues (a prefix: pairs are sorted
+  // longest first), or every pair when there are fewer (pair, query) items
+  // than narrow warps -- then each item runs nearly alone and fewer passes win
+  const int32_t npairs = packed ? (int32_t)((n_long + 1) / 2) : 0;
+  int32_t nwide = 0;
+  if ((int64_t)npairs * nq <= (int64_t)p->pair_blocks16 * PAIR_WARPS) {
+    nwide = npairs;
+  } else {
+    while (nwide < npairs && p->db->clen_h[2 * (size_t)nwide] >= p->opt.wide_min_subject) nwide++;
+  }
+  P.pair_queries = packed ? nq : 0;
+  P.n_wide_pairs = nwide;
+  if (packed) {
+    for (int32_t i = 0; i < nq; i++)
+      if (wide(hb.len[hb.order[i]])) qpair_h[n32++] = hb.order[i];
+    for (int32_t i = 0; i < nq; i++)
+      if (!wide(hb.len[hb.order[i]])) qpair_h[n32 + n16++] = hb.order[i];
+  }
+  P.qpair = p->qorder + nq;
+  P.nq_pair32 = n32;
+  P.nq_pair16 = n16;
   P.n_inter_items = (int64_t)(v.groups - gf) * nq;
   memcpy(p->qoff_h, hb.off.data(), sizeof(int64_t) * nq);
   memcpy(p->qlen_h, hb.len.data(), sizeof(int32_t) * nq);
@@ -653,7 +710,7 @@ static sw_status plan_enqueue(sw_plan* p, const HostBatch& hb, int32_t nq, int32
   if (nq > 0) {
     CUDA_TRY(cudaMemcpyAsync(p->qoff, p->qoff_h, sizeof(int64_t) * nq, cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(p->qlen, p->qlen_h, sizeof(int32_t) * nq, cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemcpyAsync(p->qorder, p->qorder_h, sizeof(int32_t) * nq, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(p->qorder, p->qorder_h, sizeof(int32_t) * 2 * nq, cudaMemcpyHostToDevice, s));
   }
   CUDA_TRY(cudaMemcpyAsync(p->params, p->params_h, sizeof(SearchParams), cudaMemcpyHostToDevice, s));
   CUDA_TRY(run_kernels(p, s));
@@ -664,7 +721,7 @@ static sw_status plan_enqueue(sw_plan* p, const HostBatch& hb, int32_t nq, int32
   p->pending.inter_items = P.n_inter_items;
   p->pending.intra_items = n_long * nq;  // (query, long subject) pairs, packed or int32
   p->pending.inter_cells = qsum * (p->db->residues - p->db->cres_h[n_long]);
-  p->pending.kernels_launched = 3;
+  p->pending.kernels_launched = 4;
   return SW_OK;
 }
 
@@ -849,6 +906,134 @@ extern "C" sw_status sw_search_plain(sw_db* db, const uint8_t* queries, const in
   cudaFree(Pd);
   cudaFree(sc);
   if (e != cudaSuccess) return sw_set_cuda_error(e, "sw_search_plain");
+  return SW_OK;
+}
+
+// ---- optimal alignments with traceback ------------------------------------------------------
+// Largest direction-bit buffer of one chunk of pairs (bytes).
+static constexpr int64_t kAlignChunkBytes = 8ll << 30;
+
+extern "C" sw_status sw_align(sw_db* db, const uint8_t* queries, const int32_t* q_lengths,
+                              int32_t n_queries, const int32_t* pair_query,
+                              const int64_t* pair_subject, int32_t n_pairs, int32_t gap_open,
+                              int32_t gap_extend, const int8_t* matrix, sw_alignment* out,
+                              uint8_t* ops, int64_t ops_capacity, void* stream) {
+  sw_clear_error();
+  if (!db) return sw_set_error(SW_EINVAL, "db is NULL");
+  if (n_pairs < 0) return sw_set_error(SW_EINVAL, "n_pairs < 0");
+  if (n_pairs > 0 && (!pair_query || !pair_subject || !out))
+    return sw_set_error(SW_EINVAL, "pair_query, pair_subject or out is NULL");
+  CUDA_TRY(cudaSetDevice(db->device));
+  HostBatch hb;
+  sw_status st = read_batch(queries, q_lengths, n_queries, hb);
+  if (st != SW_OK) return st;
+  SearchParams P;
+  memset(&P, 0, sizeof P);
+  bool packed_ok;
+  st = fill_scoring(P, gap_open, gap_extend, matrix, &packed_ok);
+  if (st != SW_OK) return st;
+  const int64_t N = db->view.n;
+  // per pair: sorted subject, sizes, and its transcript slot
+  std::vector<AlignItem> items((size_t)n_pairs);
+  std::vector<int64_t> slot((size_t)n_pairs + 1, 0);
+  for (int32_t k = 0; k < n_pairs; k++) {
+    const int32_t q = pair_query[k];
+    const int64_t sub = pair_subject[k];
+    if (q < 0 || q >= n_queries)
+      return sw_set_error(SW_EINVAL, "pair_query[%d] = %d is not a query index", k, q);
+    if (sub < 0 || sub >= N)
+      return sw_set_error(SW_EINVAL, "pair_subject[%d] = %lld is not a subject index", k,
+                          (long long)sub);
+    const int32_t s = db->sorted_of_h[(size_t)sub];
+    items[k].q = q;
+    items[k].s = s;
+    slot[k + 1] = slot[k] + hb.len[q] + db->clen_h[s];
+  }
+  if (n_pairs > 0 && slot[n_pairs] > 0 && (!ops || ops_capacity < slot[n_pairs]))
+    return sw_set_error(SW_EINVAL, "ops needs %lld bytes, has %lld", (long long)slot[n_pairs],
+                        (long long)ops_capacity);
+  if (n_pairs == 0) return SW_OK;
+  // chunks of pairs whose direction bits fit kAlignChunkBytes (one pair may exceed it alone)
+  std::vector<int32_t> chunk_begin{0};
+  int64_t words = 0, max_words = 0, max_border = 0, border = 0;
+  for (int32_t k = 0; k < n_pairs; k++) {
+    const int64_t w = align_bits_words(hb.len[items[k].q], db->clen_h[items[k].s]);
+    if (k > chunk_begin.back() && 4 * (words + w) > kAlignChunkBytes) {
+      chunk_begin.push_back(k);
+      words = border = 0;
+    }
+    items[k].bits_off = words;
+    items[k].border_off = border;
+    items[k].ops_end = slot[k + 1];
+    words += w;
+    border += db->clen_h[items[k].s];
+    max_words = std::max(max_words, words);
+    max_border = std::max(max_border, border);
+  }
+  chunk_begin.push_back(n_pairs);
+  cudaStream_t cs = (cudaStream_t)stream;
+  uint8_t* qres = nullptr;
+  int64_t* qoff = nullptr;
+  int32_t* qlen = nullptr;
+  SearchParams* Pd = nullptr;
+  AlignItem* items_d = nullptr;
+  AlignOut* out_d = nullptr;
+  uint32_t* bits = nullptr;
+  int2* border_d = nullptr;
+  uint8_t* ops_d = nullptr;
+  std::vector<AlignOut> res((size_t)n_pairs);
+  cudaError_t e = dalloc(&qres, std::max<int64_t>(hb.total, 1));
+  if (e == cudaSuccess) e = dalloc(&qoff, std::max(n_queries, 1));
+  if (e == cudaSuccess) e = dalloc(&qlen, std::max(n_queries, 1));
+  if (e == cudaSuccess) e = dalloc(&Pd, 1);
+  if (e == cudaSuccess) e = dalloc(&items_d, n_pairs);
+  if (e == cudaSuccess) e = dalloc(&out_d, n_pairs);
+  if (e == cudaSuccess) e = dalloc(&bits, std::max<int64_t>(max_words, 1));
+  if (e == cudaSuccess) e = dalloc(&border_d, std::max<int64_t>(max_border, 1));
+  if (e == cudaSuccess) e = dalloc(&ops_d, std::max<int64_t>(slot[n_pairs], 1));
+  if (e == cudaSuccess && hb.total > 0)
+    e = cudaMemcpyAsync(qres, hb.res, hb.total, cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess && n_queries > 0)
+    e = cudaMemcpyAsync(qoff, hb.off.data(), sizeof(int64_t) * n_queries, cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess && n_queries > 0)
+    e = cudaMemcpyAsync(qlen, hb.len.data(), sizeof(int32_t) * n_queries, cudaMemcpyHostToDevice, cs);
+  P.qres = qres;
+  P.qoff = qoff;
+  P.qlen = qlen;
+  P.nq = n_queries;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(Pd, &P, sizeof P, cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(items_d, items.data(), sizeof(AlignItem) * n_pairs, cudaMemcpyHostToDevice, cs);
+  for (size_t c = 0; c + 1 < chunk_begin.size() && e == cudaSuccess; c++) {
+    const int32_t k0 = chunk_begin[c], nk = chunk_begin[c + 1] - k0;
+    e = launch_align(db->view, Pd, items_d + k0, nk, bits, border_d, out_d + k0, ops_d, cs);
+    // the next chunk reuses the bits: its kernels run after this one's on the stream
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(res.data(), out_d, sizeof(AlignOut) * n_pairs, cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess && slot[n_pairs] > 0)
+    e = cudaMemcpyAsync(ops, ops_d, (size_t)slot[n_pairs], cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  cudaFree(qres);
+  cudaFree(qoff);
+  cudaFree(qlen);
+  cudaFree(Pd);
+  cudaFree(items_d);
+  cudaFree(out_d);
+  cudaFree(bits);
+  cudaFree(border_d);
+  cudaFree(ops_d);
+  if (e != cudaSuccess) return sw_set_cuda_error(e, "sw_align");
+  for (int32_t k = 0; k < n_pairs; k++) {
+    const AlignOut& r = res[k];
+    out[k].score = r.score;
+    out[k].q_begin = r.q_begin;
+    out[k].q_end = r.score > 0 ? r.i_end : 0;
+    out[k].s_begin = r.s_begin;
+    out[k].s_end = r.score > 0 ? r.j_end : 0;
+    out[k].n_ops = r.n_ops;
+    out[k].ops_offset = r.ops_offset;
+  }
   return SW_OK;
 }
 

@@ -1,4 +1,12 @@
 // pair_kernel.cu -- the packed intra-task kernel of libswgb (long subjects).
+//
+// Two widths, launched one after the other: pair_kernel<16> (16 rows per
+// lane, 512-row passes, 16 warps per SM) and pair_kernel<32> (32 rows per
+// lane, 1024-row passes, 8 warps per SM).  The wider one halves the per-step
+// overhead per cell (shuffles, residue and profile loads, loop control), so
+// it is about 15% faster per cell, but pads a query to a multiple of 1024
+// rows instead of 512.  The plan gives each query to the width with the
+// smaller padded cost (api.cu).
 #include <type_traits>
 
 #include "device_common.cuh"
@@ -20,19 +28,31 @@ namespace swgb {
 //     bottom row from this warp's border scratch and lane 31 writes it (index
 //     c is read at step c and rewritten at step c + 32*PQ - 1).
 // Residues are staged in a per-warp shared-memory ring 128 columns ahead;
-// quarter 0 loads the 16-byte profile row of its column and later quarters
-// reuse its words.  Values carry the +Go bias of the inter-task kernel, and a
+// quarter 0 loads the profile row of its column (16 bytes per 16 rows) and
+// later quarters reuse its words.  Values carry the +Go bias of the inter-task kernel, and a
 // pair half whose S' reaches the threshold is recomputed in int32 like any
 // other saturated pair.
-constexpr int PR = 16;                          // packed rows per lane
-constexpr int PQ = 4;                           // quarters (independent chains) per lane
-constexpr int PQR = PR / PQ;                    // rows per quarter
-constexpr int PAIR_PROFILE = NCODES * 32 * PR;  // int8 [code][lane][PR]
-constexpr int PRING = 384;                      // residue ring per subject: 3 blocks of 128
-constexpr int PAIR_SLICE = PAIR_PROFILE + 2 * PRING;
+constexpr int PQ = 4;                      // quarters (independent chains) per lane
+constexpr int PHALF = NCODES * 32 * 16;    // int8 [code][lane][16 rows]: one 16-row half
+constexpr int PRING = 384;                 // residue ring per subject: 3 blocks of 128
 
-__global__ void __launch_bounds__(PAIR_WARPS * 32, 4)
+// Warp slice: PR/16 profile halves (each in the conflict-free 16-byte row
+// layout of lane_profile<16>), then the two residue rings.
+template <int PR>
+struct PairShape {
+  static_assert(PR == 16 || PR == 32, "16 or 32 rows per lane");
+  static constexpr int PQR = PR / PQ;               // rows per quarter
+  static constexpr int PROFILE = (PR / 16) * PHALF;
+  static constexpr int SLICE = PROFILE + 2 * PRING;
+  static constexpr int MIN_BLOCKS = PR == 16 ? 4 : 2;  // 16 or 8 warps per SM
+};
+
+template <int PR>
+__global__ void __launch_bounds__(PAIR_WARPS * 32, PairShape<PR>::MIN_BLOCKS)
 pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scratch scr) {
+  constexpr int PQR = PairShape<PR>::PQR;
+  constexpr int PAIR_PROFILE = PairShape<PR>::PROFILE;
+  constexpr int PAIR_SLICE = PairShape<PR>::SLICE;
   extern __shared__ __align__(16) uint8_t smem[];
   int8_t* sm = (int8_t*)smem;
   load_matrix(sm, P);
@@ -47,10 +67,18 @@ pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scra
   for (int i = lane; i < 2 * PRING; i += 32) ring0[i] = PAD_CODE;
   __syncwarp();
   const int64_t warp_id = (int64_t)blockIdx.x * PAIR_WARPS + wib;
-  uint2* hb = scr.pair_border + warp_id * scr.pair_stride;
-  const int nq = P->nq;
-  if (nq <= 0) return;
-  const int64_t total = P->n_pair_items;
+  // the two widths may run at the same time: the wide one has its own rows
+  uint2* hb = scr.pair_border + ((PR == 32 ? scr.pair_rows16 : 0) + warp_id) * scr.pair_stride;
+  // Items of this width (none when the packed path is off): the wide kernel
+  // takes the pairs [0, n_wide_pairs) with the queries qpair[0, nq_pair32);
+  // the narrow one takes those pairs with qpair[nq_pair32, nq_pair32 +
+  // nq_pair16), then the other pairs with every query (qorder).
+  const int npairs = P->pair_queries > 0 ? (P->n_long + 1) / 2 : 0;
+  const int nwide = P->n_wide_pairs;
+  const int64_t first = (int64_t)nwide * (PR == 32 ? P->nq_pair32 : P->nq_pair16);
+  const int64_t total = PR == 32 ? first : first + (int64_t)(npairs - nwide) * P->pair_queries;
+  if (total <= 0) return;  // uniform over the grid
+  unsigned long long* counter = PR == 32 ? &st->pair_work32 : &st->pair_work;
   const int go = P->go;
   const uint32_t GO2 = pack2(go), NGE2 = pack2(-P->ge);
   const uint32_t MGO = (uint32_t)(-(int)((uint32_t)go * 65537u));
@@ -58,11 +86,19 @@ pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scra
   constexpr int ROWS = 32 * PR;
   for (;;) {
     unsigned long long it = 0;
-    if (lane == 0) it = atomicAdd(&st->pair_work, 1ull);
+    if (lane == 0) it = atomicAdd(counter, 1ull);
     it = __shfl_sync(FULL, it, 0);
     if ((int64_t)it >= total) break;
-    const int pair = (int)((int64_t)it / nq);
-    const int q = P->qorder[(int64_t)it % nq];
+    int pair, q;
+    if ((int64_t)it < first) {
+      const int nqw = PR == 32 ? P->nq_pair32 : P->nq_pair16;
+      pair = (int)((int64_t)it / nqw);
+      q = P->qpair[(PR == 32 ? 0 : P->nq_pair32) + (int)((int64_t)it % nqw)];
+    } else {
+      const int64_t rest = (int64_t)it - first;
+      pair = nwide + (int)(rest / P->pair_queries);
+      q = P->qorder[rest % P->pair_queries];
+    }
     const int s0 = 2 * pair, s1 = 2 * pair + 1;
     const bool has1 = s1 < P->n_long;
     const int n0 = db.clen[s0], n1 = has1 ? db.clen[s1] : 0;  // n0 >= n1 (sorted)
@@ -87,7 +123,10 @@ pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scra
     uint32_t smax = GO2;
     for (int p = 0; p < npass; p++) {
       __syncwarp();
-      lane_profile<PR>(prof, sm, qr, m, p * ROWS + lane * PR, lane);  // this lane's PR rows
+      // this lane's PR rows, 16 at a time
+      lane_profile<16>(prof, sm, qr, m, p * ROWS + lane * PR, lane);
+      if constexpr (PR == 32)
+        lane_profile<16>(prof + PHALF, sm, qr, m, p * ROWS + lane * PR + 16, lane);
       load_block(0);
       __syncwarp();
       uint32_t Hp[PR], E[PR];
@@ -107,11 +146,14 @@ pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scra
       // profile vectors of the last four steps in slot (t mod 4): quarter q at
       // step t uses word q of the vector loaded at step t - q; steps run in
       // blocks of four so every slot index is a compile-time constant
-      uint4 VA[PQ], VB[PQ];
+      // (with PR = 32 the second 16-row half in VA2 / VB2)
+      uint4 VA[PQ], VB[PQ], VA2[PQ], VB2[PQ];
 #pragma unroll
       for (int k = 0; k < PQ; k++) {
         VA[k] = make_uint4(0u, 0u, 0u, 0u);
         VB[k] = make_uint4(0u, 0u, 0u, 0u);
+        VA2[k] = make_uint4(0u, 0u, 0u, 0u);
+        VB2[k] = make_uint4(0u, 0u, 0u, 0u);
       }
       uint32_t hdiag = GO2, out_h = GO2, out_f = 0u;
       const bool last_pass = (p == npass - 1);
@@ -145,10 +187,22 @@ pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scra
         }
         const int ra = ring0[pos + U];
         const int rb = ring1[pos + U];
-        VA[U] = *(const uint4*)(prof + (ra * 32 + lane) * PR);
-        VB[U] = *(const uint4*)(prof + (rb * 32 + lane) * PR);
-        const uint32_t wa[PQ] = {VA[U].x, VA[(U + 3) & 3].y, VA[(U + 2) & 3].z, VA[(U + 1) & 3].w};
-        const uint32_t wb[PQ] = {VB[U].x, VB[(U + 3) & 3].y, VB[(U + 2) & 3].z, VB[(U + 1) & 3].w};
+        VA[U] = *(const uint4*)(prof + (ra * 32 + lane) * 16);
+        VB[U] = *(const uint4*)(prof + (rb * 32 + lane) * 16);
+        constexpr int U1 = (U + 3) & 3, U2 = (U + 2) & 3, U3 = (U + 1) & 3;
+        // words of quarter k's rows, from the vector loaded k steps ago
+        uint32_t wa[PQ][PQR / 4], wb[PQ][PQR / 4];
+        if constexpr (PR == 16) {
+          wa[0][0] = VA[U].x, wa[1][0] = VA[U1].y, wa[2][0] = VA[U2].z, wa[3][0] = VA[U3].w;
+          wb[0][0] = VB[U].x, wb[1][0] = VB[U1].y, wb[2][0] = VB[U2].z, wb[3][0] = VB[U3].w;
+        } else {
+          VA2[U] = *(const uint4*)(prof + PHALF + (ra * 32 + lane) * 16);
+          VB2[U] = *(const uint4*)(prof + PHALF + (rb * 32 + lane) * 16);
+          wa[0][0] = VA[U].x, wa[0][1] = VA[U].y, wa[1][0] = VA[U1].z, wa[1][1] = VA[U1].w;
+          wa[2][0] = VA2[U2].x, wa[2][1] = VA2[U2].y, wa[3][0] = VA2[U3].z, wa[3][1] = VA2[U3].w;
+          wb[0][0] = VB[U].x, wb[0][1] = VB[U].y, wb[1][0] = VB[U1].z, wb[1][1] = VB[U1].w;
+          wb[2][0] = VB2[U2].x, wb[2][1] = VB2[U2].y, wb[3][0] = VB2[U3].z, wb[3][1] = VB2[U3].w;
+        }
         uint32_t nh[PQ], nf[PQ];
 #pragma unroll
         for (int k = 0; k < PQ; k++) {
@@ -165,8 +219,8 @@ pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scra
             for (int i = 0; i < PQR; i++) {
               const int r = k * PQR + i;
               uint32_t e = E[r];
-              const uint32_t h = packed_cell(hd, prmt(wa[k], wb[k], sext_pair_sel(i)), e, f, GO2,
-                                             NGE2, MGO, one);
+              const uint32_t h = packed_cell(hd, prmt(wa[k][i >> 2], wb[k][i >> 2],
+                                                      sext_pair_sel(i & 3)), e, f, GO2, NGE2, MGO, one);
               hd = Hp[r];
               Hp[r] = h;
               E[r] = e;
@@ -225,23 +279,33 @@ pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scra
   }
 }
 
-size_t pair_smem_bytes() { return (size_t)MATRIX_SMEM + (size_t)PAIR_WARPS * PAIR_SLICE; }
+size_t pair_smem_bytes(int rows) {
+  const int slice = rows == 32 ? PairShape<32>::SLICE : PairShape<16>::SLICE;
+  return (size_t)MATRIX_SMEM + (size_t)PAIR_WARPS * slice;
+}
 
-int pair_blocks_per_sm() {
-  const size_t smem = pair_smem_bytes();
-  if (cudaFuncSetAttribute(pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+int pair_blocks_per_sm(int rows) {
+  if (rows != 16 && rows != 32) return 0;
+  void (*k)(DbView, const SearchParams*, SearchState*, Scratch) =
+      rows == 32 ? pair_kernel<32> : pair_kernel<16>;
+  const size_t smem = pair_smem_bytes(rows);
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return 0;
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_kernel, PAIR_WARPS * 32, smem) !=
-      cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, PAIR_WARPS * 32, smem) != cudaSuccess)
     return 0;
   return nb;
 }
 
-cudaError_t launch_pairs(int blocks, const DbView& db, const SearchParams* params,
+cudaError_t launch_pairs(int rows, int blocks, const DbView& db, const SearchParams* params,
                          SearchState* state, const Scratch& scr, cudaStream_t stream) {
-  pair_kernel<<<blocks, PAIR_WARPS * 32, pair_smem_bytes(), stream>>>(db, params, state, scr);
+  if (rows == 32)
+    pair_kernel<32><<<blocks, PAIR_WARPS * 32, pair_smem_bytes(32), stream>>>(db, params, state, scr);
+  else if (rows == 16)
+    pair_kernel<16><<<blocks, PAIR_WARPS * 32, pair_smem_bytes(16), stream>>>(db, params, state, scr);
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

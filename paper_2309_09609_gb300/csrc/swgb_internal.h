@@ -53,12 +53,17 @@ struct SearchParams {
   const int64_t* qoff;    // [nq]
   const int32_t* qlen;    // [nq]
   const int32_t* qorder;  // [nq] query indices, longest first
+  const int32_t* qpair;   // [nq_pair32 + nq_pair16] query indices for the pair kernels:
+                          // those of pair_kernel<32>, then those of pair_kernel<16>
   int32_t* scores;        // [nq x N] caller order
   int64_t n_intra_items;  // n_long x nq  (int32 intra-task items, when the packed path is off)
   int64_t n_inter_items;  // inter groups x nq  (packed inter-task items)
-  int64_t n_pair_items;   // ceil(n_long / 2) x nq  (packed intra-task items: subject pairs)
   int32_t nq;
-  int32_t n_long;         // sorted subjects [0, n_long) go to the intra-task kernel
+  int32_t pair_queries;   // nq when the packed path scores the long subjects, else 0
+  int32_t n_wide_pairs;   // subject pairs [0, n_wide_pairs) may go to pair_kernel<32> ...
+  int32_t nq_pair32;      // ... with these queries (qpair[0, nq_pair32)); the narrow
+  int32_t nq_pair16;      // kernel takes them with the others, and every other pair
+  int32_t n_long;         // sorted subjects [0, n_long) go to the intra-task kernels
   int32_t g_first;        // first inter-task group (n_long / GROUP)
   int32_t go;             // Go = gap_open + gap_extend  (Eq. 2-3)
   int32_t ge;             // Ge = gap_extend
@@ -72,7 +77,8 @@ struct SearchState {
   unsigned long long work;        // next work item (inter-task kernel)
   unsigned long long n_flags;     // saturated pairs appended to the flag list
   unsigned long long recompute;   // next flagged pair (int32 intra-task kernel, per block)
-  unsigned long long pair_work;   // next work item (packed intra-task kernel)
+  unsigned long long pair_work;   // next work item (pair_kernel<16>)
+  unsigned long long pair_work32; // next work item (pair_kernel<32>)
   unsigned long long intra_work;  // next int32 intra-task item (per warp)
   unsigned int status;            // reserved: error bits raised on the device
   unsigned int pad;
@@ -86,8 +92,10 @@ struct Scratch {
   int64_t intra_stride;       // int2 per warp
   int2* flags;                // saturated pairs: (query index, sorted subject index)
   int64_t flag_capacity;
-  uint2* pair_border;         // packed intra-task kernel, per warp: [column] (H', F') words
+  uint2* pair_border;         // packed intra-task kernels, per warp: [column] (H', F') words;
+                              // rows [0, pair_rows16) for pair_kernel<16>, the rest for <32>
   int64_t pair_stride;        // uint2 per warp
+  int64_t pair_rows16;
 };
 
 // ---- kernel launchers -----------------------------------------------------------
@@ -112,17 +120,47 @@ int intra_blocks_per_sm(int rows);
 cudaError_t launch_intra(const KernelConfig& kc, const DbView& db, const SearchParams* params,
                          SearchState* state, const Scratch& scr, cudaStream_t stream);
 
-// Packed intra-task kernel over subject pairs, long subjects (pair_kernel.cu).
+// Packed intra-task kernel over subject pairs, long subjects (pair_kernel.cu),
+// with 16 or 32 query rows per lane.
 constexpr int PAIR_WARPS = 4;  // warps per block
-int pair_blocks_per_sm();
-size_t pair_smem_bytes();
-cudaError_t launch_pairs(int blocks, const DbView& db, const SearchParams* params,
+int pair_blocks_per_sm(int rows);
+size_t pair_smem_bytes(int rows);
+cudaError_t launch_pairs(int rows, int blocks, const DbView& db, const SearchParams* params,
                          SearchState* state, const Scratch& scr, cudaStream_t stream);
+// pair_kernel<32> costs about 0.85 of pair_kernel<16> per cell it computes
+// but pads a query to 1024-row passes instead of 512: a query of m residues
+// goes to the wide kernel when 0.85 * ceil(m / 1024) * 1024 is below
+// ceil(m / 512) * 512, i.e. 17 * ceil(m / 1024) < 10 * ceil(m / 512).
+inline bool pair_wide(int32_t m) {
+  const int64_t a = ((int64_t)m + 1023) / 1024, b = ((int64_t)m + 511) / 512;
+  return m > 0 && 17 * a < 10 * b;
+}
 
 // Plain int32 baseline (Algorithm 1 per cell), one query per launch (plain_kernel.cu).
 int plain_blocks_per_sm();
 cudaError_t launch_plain(int blocks, const DbView& db, const SearchParams* params, int query,
                          int2* border, const int64_t* border_off, cudaStream_t stream);
+
+// Optimal local alignments with traceback (align_kernel.cu).
+struct AlignItem {
+  int32_t q;          // query index (SearchParams::qres / qoff / qlen)
+  int32_t s;          // sorted subject index
+  int64_t bits_off;   // first uint32 of this pair's direction bits
+  int64_t border_off; // first int2 of this pair's pass-border row
+  int64_t ops_end;    // the transcript ends just before this byte of the ops buffer
+};
+struct AlignOut {
+  int32_t score;
+  int32_t i_end, j_end;      // 1-based cell of the score (0 when it is 0)
+  int32_t q_begin, s_begin;  // 0-based first aligned residues
+  int32_t n_ops;
+  int64_t ops_offset;        // the transcript occupies [ops_offset, ops_offset + n_ops)
+};
+// uint32 words of direction bits for an m x n pair (4 bits per cell)
+int64_t align_bits_words(int32_t m, int32_t n);
+cudaError_t launch_align(const DbView& db, const SearchParams* params, const AlignItem* items,
+                         int n_items, uint32_t* bits, int2* border, AlignOut* out, uint8_t* ops,
+                         cudaStream_t stream);
 
 // Integer-pipe microbenchmark (intpeak.cu).
 int intpeak_run(int op, int blocks_per_sm, int threads, int iters, double* lane_ops_per_clk_sm,

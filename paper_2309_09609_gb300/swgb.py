@@ -37,7 +37,14 @@ class Options(ctypes.Structure):
     _fields_ = [("rows_per_thread", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
                 ("long_cutoff", ctypes.c_int32), ("intra_rows", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("force_int32", ctypes.c_int32),
-                ("auto_cutoff", ctypes.c_int32)]
+                ("auto_cutoff", ctypes.c_int32), ("wide_min_len", ctypes.c_int32),
+                ("wide_min_subject", ctypes.c_int32)]
+
+
+class Alignment(ctypes.Structure):
+    _fields_ = [("score", ctypes.c_int32), ("q_begin", ctypes.c_int32), ("q_end", ctypes.c_int32),
+                ("s_begin", ctypes.c_int32), ("s_end", ctypes.c_int32), ("n_ops", ctypes.c_int32),
+                ("ops_offset", ctypes.c_int64)]
 
 
 class Stats(ctypes.Structure):
@@ -87,6 +94,7 @@ def lib():
             "sw_search_plain": (i32, [P, P, P, i32, i32, i32, P, P, P]),
             "sw_intpeak": (i32, [i32, i32, i32, i32, P]),
             "sw_search_pairs_noalloc": (i32, [P, P, P, i32, P, P, P, i32, i32, i32, P, P, P]),
+            "sw_align": (i32, [P, P, P, i32, P, P, i32, i32, i32, P, P, P, i64, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -194,6 +202,11 @@ class Database:
         self._h = h
         self.device = device
         self.n = n
+        self._lens = np.array(lens.cpu() if hasattr(lens, "cpu") else lens, dtype=np.int32)
+
+    def subject_lengths(self) -> np.ndarray:
+        """Subject lengths in caller order (host copy)."""
+        return self._lens
 
     @classmethod
     def from_seqset(cls, ss, device: int = 0):
@@ -242,6 +255,36 @@ class Database:
         _check(lib().sw_search_plain(self._h, _ptr(q), _ptr(ql), nq, gap_open, gap_extend,
                                      _ptr(m), _ptr(out), _stream(stream)))
         return out
+
+    def align(self, queries, q_lengths, pair_query, pair_subject, gap_open=10, gap_extend=2,
+              matrix=None, stream=None) -> list[dict]:
+        """Optimal local alignments with traceback of the given (query index,
+        subject index) pairs (sw_align): per pair the score, 0-based
+        half-open ranges q[q_begin:q_end] and s[s_begin:s_end], and the
+        transcript ('M', 'I' = query residue against a gap, 'D' = subject
+        residue against a gap), first column to last."""
+        q, ql, nq = _query_args(queries, q_lengths)
+        pq = np.ascontiguousarray(pair_query, dtype=np.int32)
+        ps = np.ascontiguousarray(pair_subject, dtype=np.int64)
+        assert pq.shape == ps.shape and pq.ndim == 1
+        lens = ql.cpu().numpy() if hasattr(ql, "cpu") else np.asarray(ql)
+        if pq.size and (pq.min() < 0 or pq.max() >= nq):
+            raise SwError(SW_EINVAL, "pair_query out of range")
+        need = int(sum(int(lens[a]) for a in pq)) + int(self.subject_lengths()[ps].sum()) \
+            if pq.size else 0
+        ops = np.zeros(max(need, 1), dtype=np.uint8)
+        out = (Alignment * max(pq.size, 1))()
+        m = _matrix(matrix)
+        _check(lib().sw_align(self._h, _ptr(q), _ptr(ql), nq, _ptr(pq), _ptr(ps), pq.size,
+                              gap_open, gap_extend, _ptr(m), out, _ptr(ops), ops.size,
+                              _stream(stream)))
+        res = []
+        for k in range(pq.size):
+            r = out[k]
+            res.append({"score": r.score, "q_begin": r.q_begin, "q_end": r.q_end,
+                        "s_begin": r.s_begin, "s_end": r.s_end,
+                        "ops": ops[r.ops_offset:r.ops_offset + r.n_ops].tobytes().decode()})
+        return res
 
     def plan(self, max_queries: int, max_query_residues: int, **opts) -> "Plan":
         return Plan(self, max_queries, max_query_residues, options(**opts))

@@ -52,6 +52,7 @@ def test_options_default(lib):
     o = swgb.options()
     assert o.rows_per_thread in (16, 32) and o.intra_rows in (8, 16)
     assert o.warps_per_block >= 1 and o.long_cutoff > 0 and o.use_graph == 1
+    assert o.wide_min_len >= 0
 
 
 def test_db_create_rejects_bad_input_before_touching_the_gpu(lib):
@@ -72,6 +73,8 @@ def test_null_handles_are_rejected(lib):
     assert lib.sw_plan_create(None, 1, 1, None, ctypes.byref(z)) == swgb.SW_EINVAL
     assert lib.sw_plan_search(None, None, None, 0, 10, 2, None, None, None) == swgb.SW_EINVAL
     assert lib.sw_plan_wait(None, 0) == swgb.SW_EINVAL
+    assert lib.sw_align(None, None, None, 0, None, None, 0, 10, 2, None, None, None, 0,
+                        None) == swgb.SW_EINVAL
     lib.sw_db_destroy(None)
     lib.sw_plan_destroy(None)
     assert lib.sw_db_subjects(None) == 0

@@ -11,7 +11,7 @@ import bench  # noqa: E402
 
 def _args(**kw):
     base = dict(workload="paper-search", subjects=None, queries=None, rows=None, warps=None,
-                cutoff=None, tune=False)
+                cutoff=None, tune=False, wide_min=None, wide_min_subject=None)
     base.update(kw)
     return argparse.Namespace(**base)
 
@@ -27,7 +27,8 @@ def test_traffic_record_applies_only_to_the_profiled_kernel_and_workload():
     assert bench.profiled_traffic(_args(subjects=1000)) is None
     assert bench.profiled_traffic(_args(rows=16)) is None
     assert bench.profiled_traffic(_args(cutoff=3000)) is None
-    assert bench.profiled_traffic(_args(workload="long")) is None
+    assert bench.profiled_traffic(_args(workload="long")) is None        # not the inter kernel's
+    assert bench.profiled_traffic(_args(workload="batched-uneven"), "pair_kernel") is None
 
 
 def test_workload_query_subset():

@@ -3,7 +3,7 @@
 Each case runs the library's paths through the C ABI -- the one-shot search,
 a plan replaying its CUDA graph, and the plain int32 baseline -- and compares
 every score with the oracle (Eq. 1-3).  Sizes span several tiles and ragged
-tails: query lengths around the 16/32-row strips and the 256/512-row intra
+tails: query lengths around the 16/32-row strips and the 256/512/1024-row intra
 passes, subject lengths around the 8-residue chunks and the 64-subject groups.
 """
 import numpy as np
@@ -90,6 +90,32 @@ def test_packed_pairs_odd_count_and_unequal_lengths():
     q = seqset(rng, [1, 100, 511, 512, 513, 1100])
     res, st = all_paths(q, db, long_cutoff=100, plain=False)
     assert st["intra_items"] >= 65 * len(q)
+    assert_exact(res, oracle_all(q, db))
+
+
+def test_pair_kernel_widths_split_the_queries():
+    # Long subjects are scored by pair_kernel<32> (1024-row passes) for the
+    # queries whose padded cost is lower there -- here 513, 1000 and 3073
+    # residues -- and by pair_kernel<16> (512-row passes) for the rest: 1,
+    # 500, 1025, 1100 and 2049.  Both run several passes.
+    rng = np.random.default_rng(42)
+    db = seqset(rng, list(rng.integers(600, 2500, size=41)) + list(rng.integers(1, 300, size=70)))
+    q = seqset(rng, [1, 500, 513, 1000, 1025, 1100, 2049, 3073])
+    res, st = all_paths(q, db, long_cutoff=550, plain=False)
+    assert st["intra_items"] >= 41 * len(q)
+    assert_exact(res, oracle_all(q, db))
+
+
+def test_pair_kernel_wide_subject_prefix():
+    # More (pair, query) items than 16-row warps, so only the subject pairs
+    # whose longer subject reaches wide_min_subject may go wide: the wide
+    # kernel takes those pairs with the wide queries, the narrow one takes
+    # them with the other queries, then every shorter pair with all queries.
+    rng = np.random.default_rng(43)
+    db = seqset(rng, list(rng.integers(600, 2000, size=700)) + list(rng.integers(1, 300, size=50)))
+    q = seqset(rng, [513, 1000, 3073, 500, 1100, 700, 900, 2049])
+    res, st = all_paths(q, db, long_cutoff=550, plain=False, wide_min_subject=1300)
+    assert st["intra_items"] >= 700 * len(q)
     assert_exact(res, oracle_all(q, db))
 
 
