@@ -117,3 +117,29 @@ def test_bad_arguments_are_rejected():
     assert d.align(q.res, q.lens, [], []) == []
     # the context is still usable
     assert d.align(q.res, q.lens, [1], [1])[0]["score"] == oracle_all(q, db)[1, 1]
+
+
+def test_full_size_pair_by_properties():
+    # A 20,000 x 25,000 pair (79 passes, 0.25 GB of direction bits): too big
+    # for the full-matrix oracle, so the alignment is checked by properties
+    # that fix it at any size, with the linear-space score oracle.
+    from test_oracle_align_pins import rescore
+    rng = np.random.default_rng(15)
+    q = seqset(rng, [20000])
+    core = q.seq(0)[2000:17000].copy()
+    core[::9] = (core[::9] + 7) % 20                        # substitutions
+    core = np.delete(core, np.arange(5000, 5012))          # a 12-residue deletion
+    core = np.insert(core, 9000, rng.integers(0, 20, 30).astype(np.uint8))  # an insertion
+    d_seq = np.concatenate([rng.integers(0, 20, 4000), core, rng.integers(0, 20, 6018)])
+    db = seqset(rng, [len(d_seq)])
+    db.res = d_seq.astype(np.uint8)
+    d = swgb.Database.from_seqset(db)
+    a = d.align(q.res, q.lens, [0], [0])[0]
+    qs, ds = q.seq(0), db.seq(0)
+    s = oracle.sw_score(qs, ds)
+    assert a["score"] == s and s > 20000
+    assert rescore(qs, ds, a, oracle.blosum62(), 10, 2) == s
+    assert oracle.sw_score(qs[a["q_begin"]:a["q_end"]], ds[a["s_begin"]:a["s_end"]]) == s
+    assert oracle.sw_score(qs[:a["q_end"] - 1], ds) < s
+    assert oracle.sw_score(qs[:a["q_end"]], ds[:a["s_end"] - 1]) < s
+    assert a["ops"].count("I") >= 10 and a["ops"].count("D") >= 10   # both indels are gaps
