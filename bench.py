@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--rows", type=int, default=None, help="packed rows per thread (16/32)")
     ap.add_argument("--cutoff", type=int, default=None, help="inter/intra length cutoff")
     ap.add_argument("--warps", type=int, default=None)
+    ap.add_argument("--cols", type=int, default=None, help="inter-task wavefront columns (4/8)")
     ap.add_argument("--wide-min", type=int, default=None,
                     help="shortest query scored 32 rows per lane against long subjects")
     ap.add_argument("--wide-min-subject", type=int, default=None,
@@ -278,6 +279,7 @@ def profiled_traffic(args, kernel="inter_kernel"):
         return None
     default = (not args.subjects and not args.queries and args.rows in (None, 32)
                and args.warps in (None, 8) and args.cutoff in (None, 1500) and not args.tune
+               and getattr(args, "cols", None) in (None, 8)
                and getattr(args, "wide_min", None) is None
                and getattr(args, "wide_min_subject", None) is None)
     fname, srcs = TRAFFIC_RECORDS[key]
@@ -362,6 +364,8 @@ def run_native(args):
         opts["long_cutoff"] = args.cutoff
     if args.warps:
         opts["warps_per_block"] = args.warps
+    if args.cols:
+        opts["inter_columns"] = args.cols
     if args.no_graph:
         opts["use_graph"] = 0
     if args.wide_min is not None:

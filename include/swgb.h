@@ -108,6 +108,9 @@ typedef struct {
   int32_t wide_min_subject;  /* ... against subject pairs whose longer subject has at least
                                 this many residues, or against every pair when the search
                                 has fewer (pair, query) items than 16-row warps; default 4096 */
+  int32_t inter_columns;     /* subject columns per wavefront in the packed inter-task kernel
+                                with rows_per_thread 32: 4 or 8 (16 rows always use 4);
+                                default 8 */
 } sw_options;
 
 void sw_options_default(sw_options* opt);

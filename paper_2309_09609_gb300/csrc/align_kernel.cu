@@ -146,6 +146,159 @@ align_forward(DbView db, const SearchParams* __restrict__ P, const AlignItem* __
   }
 }
 
+// The same forward pass with a whole block per pair, for few long pairs:
+// the 16 warps take the query's passes round-robin on the stage schedule of
+// the int32 recompute (pass p starts LAG stages of 32 steps after pass p - 1,
+// every stage ends at __syncthreads, each warp writes the bottom rows of its
+// passes to its own scratch row and reads those of the pass before).  Cells,
+// bits and the end cell are exactly those of align_forward.
+constexpr int ABW = 16;   // warps per block
+constexpr int ALAG = 3;   // stages between the starts of consecutive passes
+
+__global__ void __launch_bounds__(ABW * 32)
+align_forward_block(DbView db, const SearchParams* __restrict__ P,
+                    const AlignItem* __restrict__ items, int n_items, uint32_t* __restrict__ bits,
+                    int2* __restrict__ border, AlignOut* __restrict__ out) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ int red_v[ABW], red_i[ABW], red_j[ABW];
+  int8_t* sm = (int8_t*)smem;
+  load_matrix(sm, P);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  uint8_t* prof = smem + MATRIX_SMEM + wib * (NCODES * 32 * AT);
+  const int go = P->go, ge = P->ge;
+  for (int k = blockIdx.x; k < n_items; k += gridDim.x) {  // uniform over the block
+    const AlignItem it = items[k];
+    const int m = P->qlen[it.q];
+    const int n = db.clen[it.s];
+    const uint8_t* __restrict__ qr = P->qres + P->qoff[it.q];
+    const uint8_t* __restrict__ d = db.cont + db.coff[it.s];
+    int2* own = border + it.border_off + (int64_t)wib * n;               // this warp's rows
+    const int2* src = border + it.border_off + (int64_t)((wib + ABW - 1) % ABW) * n;
+    const int npass = n > 0 ? (m + AROWS - 1) / AROWS : 0;
+    const int spass = (n + 31 + 31) / 32;
+    const int period = max(spass, ALAG * ABW);
+    const int nstages =
+        npass > 0 ? ((npass - 1) / ABW) * period + ((npass - 1) % ABW) * ALAG + spass : 0;
+    const int2 top = make_int2(0, -go);
+    int bv = 0, bi = INT32_MAX, bj = INT32_MAX;
+    int Hp[AT], E[AT], hdiag = 0, out_h = 0, out_f = -go;
+    int p = 0;
+    int2 bcur = top, bnext = top;
+    for (int g = 0; g < nstages; g++) {
+      const int rel = g - wib * ALAG;
+      int ks = -1;
+      if (rel >= 0) {
+        const int r = rel / period;
+        const int kk = rel - r * period;
+        if (kk < spass && wib + r * ABW < npass) {
+          ks = kk;
+          p = wib + r * ABW;
+        }
+      }
+      if (ks >= 0) {  // warp-uniform
+        if (ks == 0) {
+          __syncwarp();
+          lane_profile<AT>(prof, sm, qr, m, p * AROWS + lane * AT, lane);
+          __syncwarp();
+#pragma unroll
+          for (int r = 0; r < AT; r++) {
+            Hp[r] = 0;
+            E[r] = -go;
+          }
+          hdiag = 0;
+          out_h = 0;
+          out_f = -go;
+          bcur = (p > 0 && lane < n) ? src[lane] : top;
+        } else {
+          bcur = bnext;
+        }
+        const int jn = 32 * (ks + 1) + lane;
+        bnext = (p > 0 && jn < n) ? src[jn] : top;
+        const bool last_pass = (p == npass - 1);
+        const int row0 = p * AROWS + lane * AT;
+        const int t0 = 32 * ks;
+        const int tend = min(t0 + 32, n + 31);
+        for (int t = t0; t < tend; t++) {
+          int in_h = __shfl_up_sync(FULL, out_h, 1);
+          int in_f = __shfl_up_sync(FULL, out_f, 1);
+          const int bh = __shfl_sync(FULL, bcur.x, t - t0);
+          const int bf = __shfl_sync(FULL, bcur.y, t - t0);
+          if (lane == 0) {
+            in_h = bh;
+            in_f = bf;
+          }
+          const int j = t - lane;
+          if (j >= 0 && j < n) {
+            const uint2 pv = *(const uint2*)(prof + ((int)d[j] * 32 + lane) * AT);
+            int hd = hdiag;
+            hdiag = in_h;
+            int f = in_f;
+            uint32_t word = 0;
+#pragma unroll
+            for (int r = 0; r < AT; r++) {
+              const int w = sext_byte(r < 4 ? pv.x : pv.y, r & 3);
+              const int e = E[r];
+              const int diag = hd + w;
+              const int h = max(max(diag, e), max(f, 0));                // Eq. 1
+              const uint32_t srcc = h == 0 ? 0u : h == diag ? 1u : h == e ? 2u : 3u;
+              hd = Hp[r];
+              Hp[r] = h;
+              const int t_open = h - go, e_ext = e - ge, f_ext = f - ge;
+              E[r] = max(e_ext, t_open);                                 // Eq. 2
+              f = max(f_ext, t_open);                                    // Eq. 3
+              word |= (srcc | (t_open >= e_ext ? 4u : 0u) | (t_open >= f_ext ? 8u : 0u)) << (4 * r);
+              const int row = row0 + r;
+              if (h > 0 && row < m && end_before(h, row + 1, j + 1, bv, bi, bj)) {
+                bv = h;
+                bi = row + 1;
+                bj = j + 1;
+              }
+            }
+            out_h = Hp[AT - 1];
+            out_f = f;
+            bits[bits_word(it.bits_off, n, p, t, lane)] = word;
+            if (lane == 31 && !last_pass) own[j] = make_int2(out_h, out_f);
+          }
+        }
+      }
+      __syncthreads();
+    }
+    // the first cell in row-major order holding the largest H, over the block
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const int v2 = __shfl_xor_sync(FULL, bv, o);
+      const int i2 = __shfl_xor_sync(FULL, bi, o);
+      const int j2 = __shfl_xor_sync(FULL, bj, o);
+      if (end_before(v2, i2, j2, bv, bi, bj)) {
+        bv = v2;
+        bi = i2;
+        bj = j2;
+      }
+    }
+    if (lane == 0) {
+      red_v[wib] = bv;
+      red_i[wib] = bi;
+      red_j[wib] = bj;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < ABW; w++)
+        if (end_before(red_v[w], red_i[w], red_j[w], bv, bi, bj)) {
+          bv = red_v[w];
+          bi = red_i[w];
+          bj = red_j[w];
+        }
+      AlignOut r{};
+      r.score = bv;
+      r.i_end = bv > 0 ? bi : 0;
+      r.j_end = bv > 0 ? bj : 0;
+      out[k] = r;
+    }
+    __syncthreads();  // red_* are rewritten by the next pair
+  }
+}
+
 __global__ void __launch_bounds__(128)
 align_traceback(DbView db, const SearchParams* __restrict__ P, const AlignItem* __restrict__ items,
                 int n_items, const uint32_t* __restrict__ bits, AlignOut* __restrict__ out,
@@ -197,16 +350,26 @@ align_traceback(DbView db, const SearchParams* __restrict__ P, const AlignItem* 
 }
 
 cudaError_t launch_align(const DbView& db, const SearchParams* params, const AlignItem* items,
-                         int n_items, uint32_t* bits, int2* border, AlignOut* out, uint8_t* ops,
-                         cudaStream_t stream) {
+                         int n_items, bool block_mode, uint32_t* bits, int2* border, AlignOut* out,
+                         uint8_t* ops, cudaStream_t stream) {
   if (n_items <= 0) return cudaSuccess;
   int sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int blocks = std::min((n_items + ALIGN_WARPS - 1) / ALIGN_WARPS, std::max(sms, 1) * 8);
-  align_forward<<<blocks, ALIGN_WARPS * 32, 0, stream>>>(db, params, items, n_items, bits, border,
-                                                         out);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e;
+  if (block_mode) {
+    const size_t smem = (size_t)MATRIX_SMEM + (size_t)ABW * NCODES * 32 * AT;
+    e = cudaFuncSetAttribute(align_forward_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    align_forward_block<<<std::min(n_items, std::max(sms, 1)), ABW * 32, smem, stream>>>(
+        db, params, items, n_items, bits, border, out);
+  } else {
+    const int blocks = std::min((n_items + ALIGN_WARPS - 1) / ALIGN_WARPS, std::max(sms, 1) * 8);
+    align_forward<<<blocks, ALIGN_WARPS * 32, 0, stream>>>(db, params, items, n_items, bits,
+                                                           border, out);
+  }
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   align_traceback<<<(n_items + 127) / 128, 128, 0, stream>>>(db, params, items, n_items, bits, out,
                                                              ops);

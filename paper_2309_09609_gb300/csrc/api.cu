@@ -110,6 +110,7 @@ extern "C" void sw_options_default(sw_options* opt) {
   opt->auto_cutoff = 0;
   opt->wide_min_len = 0;
   opt->wide_min_subject = 4096;
+  opt->inter_columns = 8;
 }
 
 // ---- small helpers ----------------------------------------------------------------
@@ -479,6 +480,8 @@ extern "C" sw_status sw_plan_create(sw_db* db, int32_t max_queries, int64_t max_
   if (o.warps_per_block < 1 || o.warps_per_block > 8)
     return sw_set_error(SW_EINVAL, "warps_per_block must be 1..8");
   if (o.long_cutoff < 0) return sw_set_error(SW_EINVAL, "long_cutoff < 0");
+  if (o.inter_columns != 4 && o.inter_columns != 8)
+    return sw_set_error(SW_EINVAL, "inter_columns must be 4 or 8");
   if (o.wide_min_len < 0 || o.wide_min_subject < 0)
     return sw_set_error(SW_EINVAL, "wide_min_len and wide_min_subject must be >= 0");
   CUDA_TRY(cudaSetDevice(db->device));
@@ -501,13 +504,16 @@ extern "C" sw_status sw_plan_create(sw_db* db, int32_t max_queries, int64_t max_
 
   int dev_sms = 0;
   cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, db->device);
-  const int bps = inter_blocks_per_sm(o.rows_per_thread, o.warps_per_block);
+  // eight columns per wavefront need 32 rows per thread; 16 rows use four
+  const int cols = o.rows_per_thread == 32 ? o.inter_columns : 4;
+  const int bps = inter_blocks_per_sm(o.rows_per_thread, cols, o.warps_per_block);
   if (bps < 1) {
     plan_free(p);
     return sw_set_error(SW_ECUDA, "inter-task kernel cannot launch with %d warps (rows %d)",
                         o.warps_per_block, o.rows_per_thread);
   }
   p->kc.variant = o.rows_per_thread;
+  p->kc.cols = cols;
   p->kc.warps = o.warps_per_block;
   p->kc.blocks = dev_sms * bps;
   p->kc.smem = inter_smem_bytes(o.rows_per_thread, o.warps_per_block);
@@ -953,6 +959,11 @@ extern "C" sw_status sw_align(sw_db* db, const uint8_t* queries, const int32_t* 
     return sw_set_error(SW_EINVAL, "ops needs %lld bytes, has %lld", (long long)slot[n_pairs],
                         (long long)ops_capacity);
   if (n_pairs == 0) return SW_OK;
+  // few pairs: a block of 16 warps per pair; many: a warp per pair
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, db->device);
+  const bool block_mode = n_pairs <= std::max(sms, 1);
+  const int64_t border_rows = block_mode ? ALIGN_BLOCK_ROWS : 1;
   // chunks of pairs whose direction bits fit kAlignChunkBytes (one pair may exceed it alone)
   std::vector<int32_t> chunk_begin{0};
   int64_t words = 0, max_words = 0, max_border = 0, border = 0;
@@ -966,7 +977,7 @@ extern "C" sw_status sw_align(sw_db* db, const uint8_t* queries, const int32_t* 
     items[k].border_off = border;
     items[k].ops_end = slot[k + 1];
     words += w;
-    border += db->clen_h[items[k].s];
+    border += border_rows * db->clen_h[items[k].s];
     max_words = std::max(max_words, words);
     max_border = std::max(max_border, border);
   }
@@ -1006,7 +1017,8 @@ extern "C" sw_status sw_align(sw_db* db, const uint8_t* queries, const int32_t* 
     e = cudaMemcpyAsync(items_d, items.data(), sizeof(AlignItem) * n_pairs, cudaMemcpyHostToDevice, cs);
   for (size_t c = 0; c + 1 < chunk_begin.size() && e == cudaSuccess; c++) {
     const int32_t k0 = chunk_begin[c], nk = chunk_begin[c + 1] - k0;
-    e = launch_align(db->view, Pd, items_d + k0, nk, bits, border_d, out_d + k0, ops_d, cs);
+    e = launch_align(db->view, Pd, items_d + k0, nk, block_mode, bits, border_d, out_d + k0, ops_d,
+                     cs);
     // the next chunk reuses the bits: its kernels run after this one's on the stream
   }
   if (e == cudaSuccess)

@@ -108,7 +108,87 @@ __device__ __forceinline__ void packed_quad(uint32_t (&Hp)[T], uint32_t (&E)[T],
   o1 = make_uint4(bottom[2], f[2], bottom[3], f[3]);
 }
 
+// Eight adjacent columns -- a whole 8-residue chunk -- as one wavefront, for
+// T = 32: the same skew as packed_quad (column c updates row k - c at step
+// k), with up to eight independent cell updates per step.  Each column holds
+// only the 16-row half of its profile row that its current rows need,
+// loaded when the column reaches row 0 and row 16, so eight columns take the
+// profile registers of four.  b[q] / o[q] hold (H'_c, F'_c) of columns 2q and
+// 2q + 1 above / at the bottom of the strip.
 template <int T>
+__device__ __forceinline__ void packed_oct(uint32_t (&Hp)[T], uint32_t (&E)[T], uint32_t& hdiag,
+                                           uint32_t& smax, const uint8_t* slice, int p16,
+                                           const uint4& rr, const uint4 (&b)[4], uint4 (&o)[4],
+                                           uint32_t GO2, uint32_t NGE2, uint32_t MGO,
+                                           uint32_t one) {
+  static_assert(T == 32, "the eight-column wavefront is for 32 rows");
+  constexpr int HALVES = 2;
+  constexpr int W = 8;
+  uint32_t ca[W], cb[W];
+#pragma unroll
+  for (int c = 0; c < W; c++) {
+    ca[c] = ((c < 4 ? rr.x : rr.y) >> (8 * (c & 3))) & 0xffu;
+    cb[c] = ((c < 4 ? rr.z : rr.w) >> (8 * (c & 3))) & 0xffu;
+  }
+  uint4 pa[W], pb[W];
+  uint32_t htop[W], f[W], last[W], last2[W], bottom[W];
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    htop[2 * q] = b[q].x;
+    f[2 * q] = b[q].y;
+    htop[2 * q + 1] = b[q].z;
+    f[2 * q + 1] = b[q].w;
+  }
+#pragma unroll
+  for (int c = 0; c < W; c++) last[c] = last2[c] = bottom[c] = 0u;
+  uint32_t hd0 = hdiag;  // column 0's diagonal: previous column, previous row
+  hdiag = htop[W - 1];
+#pragma unroll
+  for (int k = 0; k < T + W - 1; k++) {
+    uint32_t out[W];
+#pragma unroll
+    for (int c = 0; c < W; c++) {
+      out[c] = 0u;
+      const int r = k - c;
+      if (r < 0 || r >= T) continue;
+      if ((r & 15) == 0) {  // this column enters a new 16-row half of its profile row
+        const int h = r >> 4;
+        pa[c] = *(const uint4*)(slice + (ca[c] * HALVES + h) * 128 + p16);
+        pb[c] = *(const uint4*)(slice + (cb[c] * HALVES + h) * 128 + p16);
+      }
+      uint32_t hd;
+      if (c == 0) {
+        hd = hd0;
+        hd0 = Hp[r];
+      } else {
+        hd = r == 0 ? htop[c - 1] : last2[c - 1];  // H' of column c - 1, row r - 1
+      }
+      const int wq = (r >> 2) & 3;
+      const uint32_t a32 = wq == 0 ? pa[c].x : wq == 1 ? pa[c].y : wq == 2 ? pa[c].z : pa[c].w;
+      const uint32_t b32 = wq == 0 ? pb[c].x : wq == 1 ? pb[c].y : wq == 2 ? pb[c].z : pb[c].w;
+      uint32_t e = E[r];
+      out[c] = packed_cell(hd, prmt(a32, b32, sext_pair_sel(r & 3)), e, f[c], GO2, NGE2, MGO, one);
+      E[r] = e;
+      if (c == W - 1) Hp[r] = out[c];
+      if (r == T - 1) bottom[c] = out[c];
+    }
+    // S' over this step's cells (pairs through a three-input max)
+    const int lo = k - (T - 1) > 0 ? k - (T - 1) : 0;
+    const int hi = k < W - 1 ? k : W - 1;
+    int c = lo;
+    for (; c + 1 <= hi; c += 2) smax = __vimax3_s16x2(smax, out[c], out[c + 1]);
+    if (c == hi) smax = __vmaxs2(smax, out[c]);
+#pragma unroll
+    for (int c2 = 0; c2 < W; c2++) {
+      last2[c2] = last[c2];
+      last[c2] = out[c2];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; q++) o[q] = make_uint4(bottom[2 * q], f[2 * q], bottom[2 * q + 1], f[2 * q + 1]);
+}
+
+template <int T, int WC>
 __device__ void inter_item(const DbView& db, const SearchParams* __restrict__ P, SearchState* st,
                            const int8_t* __restrict__ sm, uint8_t* slice, int lane,
                            int64_t warp_id, const Scratch& scr, int q, int g) {
@@ -194,6 +274,17 @@ __device__ void inter_item(const DbView& db, const SearchParams* __restrict__ P,
       cp_async_wait<CRING - 1>();  // chunk c has landed
       const int slot = c % CRING;
       const uint4 rr = rring[slot * 32];
+      if constexpr (WC == 8) {  // the whole chunk as one eight-column wavefront
+        const uint4 bv[4] = {bring[(slot * 4 + 0) * 32], bring[(slot * 4 + 1) * 32],
+                             bring[(slot * 4 + 2) * 32], bring[(slot * 4 + 3) * 32]};
+        uint4 ov[4];
+        packed_oct<T>(Hp, E, hdiag, smax, slice, p16, rr, bv, ov, GO2, NGE2, MGO, one);
+        if (!last) {
+#pragma unroll
+          for (int q = 0; q < 4; q++) bd[(c * 4 + q) * 32] = ov[q];
+        }
+        continue;
+      }
       // two groups of 4 columns (one residue word per subject each); for
       // T = 16 both are unrolled so the second group's profile loads can be
       // issued during the first group's wavefront tail
@@ -237,7 +328,7 @@ __device__ void inter_item(const DbView& db, const SearchParams* __restrict__ P,
   }
 }
 
-template <int T>
+template <int T, int WC>
 __global__ void __launch_bounds__(256, (T == 16 ? 2 : 1))
 inter_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scratch scr) {
   extern __shared__ __align__(16) uint8_t smem[];
@@ -257,15 +348,16 @@ inter_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scr
     if ((int64_t)it >= total) break;
     const int g = P->g_first + (int)((int64_t)it / nq);
     const int q = P->qorder[(int64_t)it % nq];
-    inter_item<T>(db, P, st, sm, slice, lane, warp_id, scr, q, g);
+    inter_item<T, WC>(db, P, st, sm, slice, lane, warp_id, scr, q, g);
   }
 }
 
 typedef void (*InterKernel)(DbView, const SearchParams*, SearchState*, Scratch);
 
-static InterKernel pick_inter(int rows) {
-  if (rows == 16) return inter_kernel<16>;
-  if (rows == 32) return inter_kernel<32>;
+static InterKernel pick_inter(int rows, int cols) {
+  if (rows == 16 && cols == 4) return inter_kernel<16, 4>;
+  if (rows == 32 && cols == 4) return inter_kernel<32, 4>;
+  if (rows == 32 && cols == 8) return inter_kernel<32, 8>;
   return nullptr;
 }
 
@@ -274,8 +366,8 @@ size_t inter_smem_bytes(int rows, int warps) {
   return (size_t)MATRIX_SMEM + (size_t)warps * slice;
 }
 
-int inter_blocks_per_sm(int rows, int warps) {
-  InterKernel k = pick_inter(rows);
+int inter_blocks_per_sm(int rows, int cols, int warps) {
+  InterKernel k = pick_inter(rows, cols);
   if (!k || warps < 1 || warps > 8) return 0;
   const size_t smem = inter_smem_bytes(rows, warps);
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -291,7 +383,7 @@ cudaError_t launch_inter(const KernelConfig& kc, const DbView& db, const SearchP
                          SearchState* state, const Scratch& scr, cudaStream_t stream) {
   // the dynamic shared-memory attribute was set by inter_blocks_per_sm when
   // the plan was created; nothing here may be an unsafe call under capture
-  InterKernel k = pick_inter(kc.variant);
+  InterKernel k = pick_inter(kc.variant, kc.cols);
   if (!k) return cudaErrorInvalidValue;
   k<<<kc.blocks, kc.warps * 32, kc.smem, stream>>>(db, params, state, scr);
   return cudaGetLastError();

@@ -101,6 +101,7 @@ struct Scratch {
 // ---- kernel launchers -----------------------------------------------------------
 struct KernelConfig {
   int variant;     // inter: packed rows per thread (16/32); intra: int32 rows per lane (8/16)
+  int cols;        // inter: columns per wavefront (4, or 8 with 32 rows)
   int warps;       // warps per block
   int blocks;      // grid size
   size_t smem;     // dynamic shared memory per block
@@ -108,7 +109,7 @@ struct KernelConfig {
 
 // Inter-task kernel, packed 16-bit (inter_kernel.cu).
 size_t inter_smem_bytes(int rows, int warps);
-int inter_blocks_per_sm(int rows, int warps);  // resident blocks per SM, 0 if it cannot launch
+int inter_blocks_per_sm(int rows, int cols, int warps);  // resident blocks per SM, 0 if none
 cudaError_t launch_inter(const KernelConfig& kc, const DbView& db, const SearchParams* params,
                          SearchState* state, const Scratch& scr, cudaStream_t stream);
 
@@ -158,9 +159,12 @@ struct AlignOut {
 };
 // uint32 words of direction bits for an m x n pair (4 bits per cell)
 int64_t align_bits_words(int32_t m, int32_t n);
+// block_mode: one block of 16 warps per pair (border: 16 rows of the subject's
+// length per pair), else one warp per pair (one row per pair)
 cudaError_t launch_align(const DbView& db, const SearchParams* params, const AlignItem* items,
-                         int n_items, uint32_t* bits, int2* border, AlignOut* out, uint8_t* ops,
-                         cudaStream_t stream);
+                         int n_items, bool block_mode, uint32_t* bits, int2* border, AlignOut* out,
+                         uint8_t* ops, cudaStream_t stream);
+constexpr int ALIGN_BLOCK_ROWS = 16;  // border rows per pair in block mode
 
 // Integer-pipe microbenchmark (intpeak.cu).
 int intpeak_run(int op, int blocks_per_sm, int threads, int iters, double* lane_ops_per_clk_sm,

@@ -1,8 +1,8 @@
 """Autotuner for the search plan's tile shape.
 
-Candidates: query rows per thread of the packed kernel (16, 32), warps per
-block (4, 8), the inter/intra length cutoff, and rows per lane of the int32
-intra-task kernel (8, 16).  None of them changes a score; they change speed
+Candidates: query rows per thread of the packed kernel (16, 32), columns per
+wavefront with 32 rows (4, 8), warps per block (4, 8), the inter/intra length
+cutoff, and rows per lane of the int32 intra-task kernel (8, 16).  None of them changes a score; they change speed
 only.  Each candidate runs a plan over a length-stratified sample of the
 batch's queries against the whole resident database and is timed by the
 plan's own CUDA events (search + recompute kernels).  The best is cached in
@@ -25,6 +25,7 @@ ROWS = (16, 32)
 WARPS = (4, 8)
 CUTOFFS = (1500, 3000, 7000, 1 << 30)
 INTRA_ROWS = (8, 16)
+COLS = (4, 8)
 _lock = threading.Lock()
 
 
@@ -38,15 +39,19 @@ def sample_queries(queries, k: int = 8):
     return queries.subset(idx), idx
 
 
-def candidates(db: swgb.Database, rows=ROWS, warps=WARPS, cutoffs=CUTOFFS, intra_rows=INTRA_ROWS):
-    """Distinct option sets: cutoffs at or above the longest subject are one."""
+def candidates(db: swgb.Database, rows=ROWS, warps=WARPS, cutoffs=CUTOFFS, intra_rows=INTRA_ROWS,
+               cols=COLS):
+    """Distinct option sets: cutoffs at or above the longest subject are one,
+    and 16 rows per thread have one column count (4)."""
     maxlen = db.max_length
     cuts = sorted({c if c < maxlen else 1 << 30 for c in cutoffs})
     out = []
     for r, w, c in itertools.product(rows, warps, cuts):
         irs = intra_rows if c < maxlen else intra_rows[:1]
         for ir in irs:
-            out.append(dict(rows_per_thread=r, warps_per_block=w, long_cutoff=c, intra_rows=ir))
+            for k in (cols if r == 32 else (4,)):
+                out.append(dict(rows_per_thread=r, warps_per_block=w, long_cutoff=c, intra_rows=ir,
+                                inter_columns=k))
     return out
 
 

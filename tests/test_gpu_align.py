@@ -66,6 +66,20 @@ def test_many_ties_small_alphabet(alpha):
         check(q, db, pq, ps, gaps, m)
 
 
+def test_many_pairs_one_warp_each():
+    # more pairs than SMs: one warp per pair (fewer pairs get a block each,
+    # as in the other tests); both must give the same alignments
+    rng = np.random.default_rng(16)
+    q = seqset(rng, rng.integers(1, 400, size=20))
+    db = seqset(rng, rng.integers(1, 400, size=40))
+    pq = np.repeat(np.arange(len(q)), 20)
+    ps = rng.integers(0, len(db), size=pq.size)
+    got = check(q, db, pq, ps)
+    assert len(got) == 400
+    d = swgb.Database.from_seqset(db)
+    assert d.align(q.res, q.lens, pq[:5], ps[:5]) == got[:5]       # block per pair
+
+
 def test_scores_equal_the_search_and_zero_scores():
     rng = np.random.default_rng(12)
     q = concat(seqset(rng, [0, 5, 300]), from_text("PPPP"))

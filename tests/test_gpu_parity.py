@@ -48,13 +48,13 @@ def test_plain_small_workload():
     assert st["cells"] == w.cells
 
 
-@pytest.mark.parametrize("rows", [16, 32])
+@pytest.mark.parametrize("rows,cols", [(16, 4), (32, 4), (32, 8)])
 @pytest.mark.parametrize("gaps", [(10, 2), (5, 1), (0, 1), (11, 1), (0, 0)])
-def test_ragged_tiles(rows, gaps):
+def test_ragged_tiles(rows, cols, gaps):
     rng = np.random.default_rng(rows * 100 + gaps[0] * 7 + gaps[1])
     db = seqset(rng, list(range(0, 10)) + list(rng.integers(0, 300, size=503)))
     q = seqset(rng, [0, 1, 5, 15, 16, 17, 31, 32, 33, 250])
-    res, _ = all_paths(q, db, *gaps, rows_per_thread=rows)
+    res, _ = all_paths(q, db, *gaps, rows_per_thread=rows, inter_columns=cols)
     assert_exact(res, oracle_all(q, db, *gaps))
 
 
@@ -152,6 +152,20 @@ def test_saturation_is_recomputed_exactly():
     want = oracle_all(q, db)
     assert want.max() > 32767
     res, st = all_paths(q, db, long_cutoff=4000)  # every group on the packed path
+    assert st["recomputed_pairs"] >= 6
+    assert_exact(res, want)
+
+
+def test_saturation_with_eight_column_wavefront():
+    # the 16-bit overflow guard and the int32 recompute with the inter-task
+    # kernel's eight-column wavefront
+    rng = np.random.default_rng(9)
+    w = lambda k: "W" * k
+    q = from_text(w(3100), w(2978) + "A" * 50, "HEAGAWGHEE")
+    subj = from_text(w(2977), w(2978), w(2990), w(3000) + "K" * 20, "PAWHEAE")
+    db = concat(subj, seqset(rng, rng.integers(10, 300, size=100)))
+    want = oracle_all(q, db)
+    res, st = all_paths(q, db, long_cutoff=4000, inter_columns=8)
     assert st["recomputed_pairs"] >= 6
     assert_exact(res, want)
 
