@@ -47,3 +47,25 @@ def test_two_gloo_ranks_reduce_max_time():
     for rank, (p, out) in enumerate(zip(procs, outs)):
         assert p.returncode == 0, out
         assert f"ok {rank}" in out
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    # bench.py --impl reference under two ranks: rank 0 times the oracle and
+    # prints the one JSON line; rank 1 exits 0 without work or output
+    import json
+    port = _free_port()
+    procs = []
+    for rank in range(2):
+        env = dict(os.environ, RANK=str(rank), LOCAL_RANK=str(rank), WORLD_SIZE="2",
+                   MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), SWGB_BENCH_BACKEND="gloo")
+        procs.append(subprocess.Popen(
+            [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+             "--workload", "plain-small", "--steps", "1", "--warmup", "0", "--ref-cells", "2e7"],
+            env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True))
+    outs = [p.communicate(timeout=300) for p in procs]
+    for p, (out, err) in zip(procs, outs):
+        assert p.returncode == 0, err
+    line = json.loads(outs[0][0].strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+    assert outs[1][0].strip() == ""
