@@ -73,7 +73,7 @@ void sw_default_matrix(int8_t* out);
  *   device:   CUDA device ordinal.
  * The subjects are sorted by length and laid out twice on the device: in
  * groups of 64 subjects interleaved 8 residues at a time (inter-task kernel)
- * and contiguously (intra-task and recompute kernels).  Inputs are copied;
+ * and contiguously (pair, int32 intra-task and alignment kernels).  Inputs are copied;
  * the handle owns all device memory until sw_db_destroy.
  * Errors: SW_EINVAL for a code >= 24, a negative length or n_subjects < 0;
  * SW_ENOMEM; SW_ECUDA. */
