@@ -111,6 +111,10 @@ typedef struct {
   int32_t inter_columns;     /* subject columns per wavefront in the packed inter-task kernel
                                 with rows_per_thread 32: 4 or 8 (16 rows always use 4);
                                 default 8 */
+  int32_t overlap_kernels;   /* 1: the inter-task kernel runs alongside the pair kernels
+                                instead of after them, so its blocks take the SMs that their
+                                tails leave (lower latency for small searches); search_ms and
+                                pair_ms then overlap, both from the start; default 0 */
 } sw_options;
 
 void sw_options_default(sw_options* opt);

@@ -111,6 +111,7 @@ extern "C" void sw_options_default(sw_options* opt) {
   opt->wide_min_len = 0;
   opt->wide_min_subject = 4096;
   opt->inter_columns = 8;
+  opt->overlap_kernels = 0;
 }
 
 // ---- small helpers ----------------------------------------------------------------
@@ -422,8 +423,9 @@ struct sw_plan {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   // the two pair-kernel widths run on two streams: fork after the reset, join
   // before the inter-task kernel
-  cudaStream_t side = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaStream_t side = nullptr, side2 = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr, join2 = nullptr;
+  cudaEvent_t ev_join = nullptr;  // overlap: after the pair and inter-task kernels
   bool in_flight = false;
   sw_stats stats{};
   sw_stats pending{};
@@ -440,7 +442,10 @@ static void plan_free(sw_plan* p) {
     if (e) cudaEventDestroy(e);
   if (p->fork) cudaEventDestroy(p->fork);
   if (p->join) cudaEventDestroy(p->join);
+  if (p->join2) cudaEventDestroy(p->join2);
+  if (p->ev_join) cudaEventDestroy(p->ev_join);
   if (p->side) cudaStreamDestroy(p->side);
+  if (p->side2) cudaStreamDestroy(p->side2);
   cudaFree(p->qres);
   cudaFree(p->qoff);
   cudaFree(p->qlen);
@@ -569,6 +574,9 @@ extern "C" sw_status sw_plan_create(sw_db* db, int32_t max_queries, int64_t max_
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->side2, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->join2, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreate(&p->ev_join);
   if (e != cudaSuccess) {
     sw_status st = sw_set_cuda_error(e, "sw_plan_create: allocation");
     plan_free(p);
@@ -606,11 +614,26 @@ static cudaError_t enqueue_kernels(sw_plan* p, cudaStream_t s, bool capturing) {
   if (e == cudaSuccess) e = cudaStreamWaitEvent(p->side, p->fork, 0);
   if (e == cudaSuccess) e = launch_pairs(32, p->pair_blocks32, p->db->view, p->params, p->state, p->scr, p->side);
   if (e == cudaSuccess) e = launch_pairs(16, p->pair_blocks16, p->db->view, p->params, p->state, p->scr, s);
+  if (p->opt.overlap_kernels) {
+    // the inter-task kernel too, on a third stream and issued after the pair
+    // kernels: one of its blocks needs a whole SM's registers, so it starts on
+    // an SM when the pair blocks there run out of work, and no SM idles in
+    // their tails
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->side2, p->fork, 0);
+    if (e == cudaSuccess) e = launch_inter(p->kc, p->db->view, p->params, p->state, p->scr, p->side2);
+    if (e == cudaSuccess) e = record(p->ev[2], p->side2, capturing);
+    if (e == cudaSuccess) e = cudaEventRecord(p->join2, p->side2);
+  }
   if (e == cudaSuccess) e = cudaEventRecord(p->join, p->side);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->join, 0);
   if (e == cudaSuccess) e = record(p->ev[1], s, capturing);
-  if (e == cudaSuccess) e = launch_inter(p->kc, p->db->view, p->params, p->state, p->scr, s);
-  if (e == cudaSuccess) e = record(p->ev[2], s, capturing);
+  if (p->opt.overlap_kernels) {
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->join2, 0);
+    if (e == cudaSuccess) e = record(p->ev_join, s, capturing);
+  } else {
+    if (e == cudaSuccess) e = launch_inter(p->kc, p->db->view, p->params, p->state, p->scr, s);
+    if (e == cudaSuccess) e = record(p->ev[2], s, capturing);
+  }
   if (e == cudaSuccess) e = launch_intra(p->ikc, p->db->view, p->params, p->state, p->scr, s);
   if (e == cudaSuccess) e = record(p->ev[3], s, capturing);
   return e;
@@ -733,9 +756,12 @@ static sw_status plan_enqueue(sw_plan* p, const HostBatch& hb, int32_t nq, int32
 
 static void finish_stats(sw_plan* p) {
   p->stats = p->pending;
+  // with overlap_kernels the pair and inter-task kernels both start at ev[0]
+  const bool ov = p->opt.overlap_kernels != 0;
   if (cudaEventElapsedTime(&p->stats.pair_ms, p->ev[0], p->ev[1]) != cudaSuccess ||
-      cudaEventElapsedTime(&p->stats.search_ms, p->ev[1], p->ev[2]) != cudaSuccess ||
-      cudaEventElapsedTime(&p->stats.recompute_ms, p->ev[2], p->ev[3]) != cudaSuccess) {
+      cudaEventElapsedTime(&p->stats.search_ms, ov ? p->ev[0] : p->ev[1], p->ev[2]) != cudaSuccess ||
+      cudaEventElapsedTime(&p->stats.recompute_ms, ov ? p->ev_join : p->ev[2], p->ev[3]) !=
+          cudaSuccess) {
     cudaGetLastError();
     p->stats.pair_ms = p->stats.search_ms = p->stats.recompute_ms = -1.f;
   }

@@ -38,7 +38,8 @@ class Options(ctypes.Structure):
                 ("long_cutoff", ctypes.c_int32), ("intra_rows", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("force_int32", ctypes.c_int32),
                 ("auto_cutoff", ctypes.c_int32), ("wide_min_len", ctypes.c_int32),
-                ("wide_min_subject", ctypes.c_int32), ("inter_columns", ctypes.c_int32)]
+                ("wide_min_subject", ctypes.c_int32), ("inter_columns", ctypes.c_int32),
+                ("overlap_kernels", ctypes.c_int32)]
 
 
 class Alignment(ctypes.Structure):

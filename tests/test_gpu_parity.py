@@ -119,6 +119,22 @@ def test_pair_kernel_wide_subject_prefix():
     assert_exact(res, oracle_all(q, db))
 
 
+@pytest.mark.parametrize("wide_min_subject", [0, 1 << 30])
+def test_overlapped_kernels(wide_min_subject):
+    # overlap_kernels: the inter-task kernel runs alongside the two pair
+    # kernels; same scores, and a saturated pair still goes to the recompute
+    rng = np.random.default_rng(44)
+    w = lambda k: "W" * k
+    db = concat(from_text(w(2990), w(700)), seqset(rng, list(rng.integers(600, 2500, size=60)) +
+                                                    list(rng.integers(1, 400, size=300))))
+    q = concat(from_text(w(3000)), seqset(rng, [1, 300, 513, 1000, 2049, 3073]))
+    want = oracle_all(q, db)
+    res, st = all_paths(q, db, long_cutoff=550, plain=False, overlap_kernels=1,
+                        wide_min_subject=wide_min_subject)
+    assert st["recomputed_pairs"] >= 1 and st["inter_items"] > 0 and st["intra_items"] > 0
+    assert_exact(res, want)
+
+
 def test_saturation_through_the_pair_kernel():
     rng = np.random.default_rng(41)
     q = from_text("W" * 3100, "HEAGAWGHEE" * 30)
