@@ -163,10 +163,13 @@ pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scra
       // one step of the wavefront; CHECK: some quarter may lie outside the
       // columns (ramp-up and drain); in the steady state every quarter of
       // every lane is inside, so the step needs no per-quarter test
-      auto step = [&](const int t, auto checked, auto slot) {
+      // CHECK: some quarter may lie outside the columns (ramp and drain);
+      // RING: this step may start a 128-column residue block (the steady
+      // state runs whole blocks and refills the ring before each)
+      auto step = [&](const int t, auto checked, auto slot, auto ring) {
         constexpr bool CHECK = decltype(checked)::value;
         constexpr int U = decltype(slot)::value;  // t mod 4
-        if constexpr (U == 0) {
+        if constexpr (U == 0 && decltype(ring)::value) {
           if ((t & 127) == 0) {
             load_block((t >> 7) + 1);
             __syncwarp();
@@ -175,7 +178,17 @@ pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scra
         uint32_t in_h = __shfl_up_sync(FULL, out_h, 1);
         uint32_t in_f = __shfl_up_sync(FULL, out_f, 1);
         const int c0 = t - PQ * lane;  // quarter 0's column
-        if (lane == 0) {
+        if constexpr (PR == 32) {
+          // lane 0's top border, column t, from the previous pass (unused on
+          // the first): every lane loads the same (clamped, so in bounds)
+          // word, so the load is one broadcast and no lane branches
+          const uint2 bv = hb[min(t, n0 - 1)];
+          const bool from_scratch = p > 0 && t < n0;
+          if (lane == 0) {
+            in_h = from_scratch ? bv.x : GO2;  // else H(0, j) = 0
+            in_f = from_scratch ? bv.y : 0u;   // else F(1, j) = -Go
+          }
+        } else if (lane == 0) {
           if (p > 0 && c0 < n0) {
             const uint2 v = hb[c0];
             in_h = v.x;
@@ -246,20 +259,35 @@ pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scra
           qf1[k] = nf[k];
         }
       };
-      auto block = [&](const int t0, auto checked) {
-        step(t0, checked, std::integral_constant<int, 0>{});
-        step(t0 + 1, checked, std::integral_constant<int, 1>{});
-        step(t0 + 2, checked, std::integral_constant<int, 2>{});
-        step(t0 + 3, checked, std::integral_constant<int, 3>{});
+      auto block = [&](const int t0, auto checked, auto ring) {
+        step(t0, checked, std::integral_constant<int, 0>{}, ring);
+        step(t0 + 1, checked, std::integral_constant<int, 1>{}, ring);
+        step(t0 + 2, checked, std::integral_constant<int, 2>{}, ring);
+        step(t0 + 3, checked, std::integral_constant<int, 3>{}, ring);
         pos = pos + 4 == PRING ? 0 : pos + 4;
       };
       // every quarter of every lane is inside the columns for 32*PQ-1 <= t < n0;
       // the last block may run past `steps`, where every quarter is outside
       int t0 = 0;
-      for (; t0 < 32 * PQ; t0 += 4) block(t0, std::true_type{});
+      for (; t0 < 32 * PQ; t0 += 4) block(t0, std::true_type{}, std::true_type{});
+      if constexpr (PR == 32) {
+        // steady state in whole 128-column residue blocks (t0 is a multiple
+        // of 128 here): refill the ring once, then 32 four-step blocks with
+        // no test; the rest (under 128 steady steps, then the drain) runs the
+        // checked step, so the step has two instantiations in all
+        static_assert(32 * PQ == 128, "the ramp must end on a residue block boundary");
 #pragma unroll 1
-      for (; t0 + 4 <= n0; t0 += 4) block(t0, std::false_type{});
-      for (; t0 < steps; t0 += 4) block(t0, std::true_type{});
+        for (; t0 + 128 <= n0; t0 += 128) {
+          load_block((t0 >> 7) + 1);
+          __syncwarp();
+#pragma unroll 1
+          for (int b = 0; b < 128; b += 4) block(t0 + b, std::false_type{}, std::false_type{});
+        }
+      } else {
+#pragma unroll 1
+        for (; t0 + 4 <= n0; t0 += 4) block(t0, std::false_type{}, std::true_type{});
+      }
+      for (; t0 < steps; t0 += 4) block(t0, std::true_type{}, std::true_type{});
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) smax = __vmaxs2(smax, __shfl_xor_sync(FULL, smax, o));
