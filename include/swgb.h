@@ -131,7 +131,8 @@ typedef struct {
   float recompute_ms;        /* device time of the int32 intra-task kernel (CUDA events):
                                 the recompute of saturated pairs, or every pair when the
                                 packed path is off */
-  float pair_ms;             /* device time of the packed intra-task kernel (CUDA events) */
+  float pair_ms;             /* device time of the packed intra-task kernels, both widths,
+                                from their fork to their join (CUDA events) */
   int32_t pad_;
   int64_t inter_cells;       /* cells scored by the inter-task kernel */
 } sw_stats;
@@ -147,14 +148,17 @@ sw_status sw_plan_create(sw_db* db, int32_t max_queries, int64_t max_query_resid
 void sw_plan_destroy(sw_plan* plan);
 
 /* Exact scores of every query against every subject (Eq. 1-3), the batched
- * path: three persistent launches, each taking its work longest first from
- * an atomic counter -- the packed intra-task kernel over pairs of subjects
- * longer than opt.long_cutoff, the packed inter-task kernel over (query,
- * group of 64 subjects) items, both scoring two subjects per 32-bit word in
- * 16 bits, and the int32 intra-task kernel, which recomputes every pair whose
- * 16-bit score may have saturated (one block per pair).  With gap penalties
- * too large for 16 bits, or opt.force_int32, every pair goes to the int32
- * kernel instead.  The launch sequence is replayed from a CUDA graph when
+ * path: four persistent launches, each taking its work longest first from
+ * its own atomic counter -- the packed intra-task kernel over (pair of
+ * subjects longer than opt.long_cutoff, query) items, at 32 and at 16 query
+ * rows per lane, the two launches side by side on two streams (opt.
+ * wide_min_len and opt.wide_min_subject split the items between them); then
+ * the packed inter-task kernel over (query, group of 64 subjects) items --
+ * all three scoring two subjects per 32-bit word in 16 bits -- and last the
+ * int32 intra-task kernel, which recomputes every pair whose 16-bit score may
+ * have saturated (one block per pair).  With gap penalties too large for 16
+ * bits, or opt.force_int32, every pair goes to the int32 kernel instead (one
+ * warp per pair).  The launch sequence is replayed from a CUDA graph when
  * opt.use_graph is set.
  *   queries:   concatenated query codes (sum(q_lengths) bytes), host or device.
  *   q_lengths: n_queries int32, host or device.
