@@ -119,9 +119,11 @@ def _ptr(x):
     if x is None:
         return None
     if hasattr(x, "data_ptr"):
-        assert x.is_contiguous(), "tensor must be contiguous"
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
         return ctypes.c_void_p(x.data_ptr())
-    assert isinstance(x, np.ndarray) and x.flags.c_contiguous, "need a contiguous numpy array"
+    if not (isinstance(x, np.ndarray) and x.flags.c_contiguous):
+        raise ValueError("need a contiguous numpy array")
     return ctypes.c_void_p(x.ctypes.data)
 
 
@@ -133,27 +135,64 @@ def _stream(stream):
     return ctypes.c_void_p(int(stream))
 
 
-def _u8(x):
+def _as(x, dtype: str):
+    """x as a contiguous array of `dtype` ("uint8", "int8", "int32", "int64"):
+    numpy input becomes a numpy array, a torch tensor stays a tensor on its
+    own device (converted there when its dtype differs)."""
     if hasattr(x, "data_ptr"):
-        return x
-    return np.ascontiguousarray(x, dtype=np.uint8)
+        if str(x.dtype) != "torch." + dtype:
+            x = x.to(getattr(__import__("torch"), dtype))
+        return x.contiguous()
+    return np.ascontiguousarray(x, dtype=getattr(np, dtype))
+
+
+def _host(x, dtype: str) -> np.ndarray:
+    """x as a contiguous host numpy array of `dtype` (torch tensors are copied
+    to the host), for arguments the library reads on the host."""
+    if hasattr(x, "data_ptr"):
+        x = x.detach().cpu().numpy()
+    return np.ascontiguousarray(x, dtype=getattr(np, dtype))
+
+
+def _u8(x):
+    return _as(x, "uint8")
 
 
 def _i32(x):
-    if hasattr(x, "data_ptr"):
-        return x
-    return np.ascontiguousarray(x, dtype=np.int32)
+    return _as(x, "int32")
 
 
 def _matrix(m):
+    """A 24 x 24 substitution matrix as 576 int8 (NULL, i.e. BLOSUM62, for None)."""
     if m is None:
         return None
     if hasattr(m, "data_ptr"):
-        return m
+        if m.numel() != 576:
+            raise ValueError("matrix must be 24 x 24")
+        if str(m.dtype) != "torch.int8":
+            raise TypeError("a matrix tensor must be int8")
+        return m.contiguous()
     m = np.ascontiguousarray(m)
-    assert m.size == 576, "matrix must be 24 x 24"
-    assert m.min() >= -128 and m.max() <= 127, "matrix entries must fit int8"
+    if m.size != 576:
+        raise ValueError("matrix must be 24 x 24")
+    if m.min() < -128 or m.max() > 127:
+        raise ValueError("matrix entries must fit int8")
     return np.ascontiguousarray(m.astype(np.int8).reshape(576))
+
+
+def _scores_out(out, nq: int, ns: int):
+    """The caller's score buffer (int32, nq x ns, contiguous), or a new host
+    array when out is None."""
+    if out is None:
+        return np.empty((nq, ns), dtype=np.int32)
+    if hasattr(out, "data_ptr"):
+        ok = str(out.dtype) == "torch.int32" and out.numel() == nq * ns and out.is_contiguous()
+    else:
+        ok = (isinstance(out, np.ndarray) and out.dtype == np.int32 and out.size == nq * ns
+              and out.flags.c_contiguous and out.flags.writeable)
+    if not ok:
+        raise ValueError(f"out must be a contiguous, writable int32 buffer of {nq} x {ns}")
+    return out
 
 
 def encode(text: str) -> np.ndarray:
@@ -193,17 +232,18 @@ class Database:
     """A protein database resident on one GPU (sw_db_create)."""
 
     def __init__(self, residues, lengths, device: int = 0):
-        res = _u8(residues)
-        lens = _i32(lengths)
+        # sw_db_create reads both arrays on the host
+        res = _host(residues, "uint8").reshape(-1)
+        lens = _host(lengths, "int32").reshape(-1)
         n = int(lens.shape[0])
-        if isinstance(res, np.ndarray) and res.size == 0:
+        if res.size == 0:
             res = np.zeros(1, np.uint8)
         h = ctypes.c_void_p()
         _check(lib().sw_db_create(_ptr(res), _ptr(lens) if n else None, n, device, ctypes.byref(h)))
         self._h = h
         self.device = device
         self.n = n
-        self._lens = np.array(lens.cpu() if hasattr(lens, "cpu") else lens, dtype=np.int32)
+        self._lens = lens.copy()
 
     def subject_lengths(self) -> np.ndarray:
         """Subject lengths in caller order (host copy)."""
@@ -233,9 +273,7 @@ class Database:
         return int(lib().sw_db_max_length(self._h))
 
     def _out(self, nq, out):
-        if out is None:
-            out = np.empty((nq, self.n), dtype=np.int32)
-        return out
+        return _scores_out(out, nq, self.n)
 
     def search(self, queries, q_lengths, gap_open=10, gap_extend=2, matrix=None, out=None,
                stream=None):
@@ -265,12 +303,15 @@ class Database:
         transcript ('M', 'I' = query residue against a gap, 'D' = subject
         residue against a gap), first column to last."""
         q, ql, nq = _query_args(queries, q_lengths)
-        pq = np.ascontiguousarray(pair_query, dtype=np.int32)
-        ps = np.ascontiguousarray(pair_subject, dtype=np.int64)
-        assert pq.shape == ps.shape and pq.ndim == 1
-        lens = ql.cpu().numpy() if hasattr(ql, "cpu") else np.asarray(ql)
+        pq = _host(pair_query, "int32")
+        ps = _host(pair_subject, "int64")
+        if pq.ndim != 1 or pq.shape != ps.shape:
+            raise ValueError("pair_query and pair_subject must be 1-D and of one length")
+        lens = _host(ql, "int32")
         if pq.size and (pq.min() < 0 or pq.max() >= nq):
             raise SwError(SW_EINVAL, "pair_query out of range")
+        if ps.size and (ps.min() < 0 or ps.max() >= self.n):
+            raise SwError(SW_EINVAL, "pair_subject out of range")
         need = int(sum(int(lens[a]) for a in pq)) + int(self.subject_lengths()[ps].sum()) \
             if pq.size else 0
         ops = np.zeros(max(need, 1), dtype=np.uint8)
@@ -319,8 +360,7 @@ class Plan:
     def search(self, queries, q_lengths, gap_open=10, gap_extend=2, matrix=None, out=None,
                stream=None):
         q, ql, nq = _query_args(queries, q_lengths)
-        if out is None:
-            out = np.empty((nq, self.db.n), dtype=np.int32)
+        out = _scores_out(out, nq, self.db.n)
         m = _matrix(matrix)
         _check(lib().sw_plan_search(self._h, _ptr(q), _ptr(ql), nq, gap_open, gap_extend,
                                     _ptr(m), _ptr(out), _stream(stream)))
@@ -328,8 +368,10 @@ class Plan:
 
     def search_async(self, queries, q_lengths, out, gap_open=10, gap_extend=2, matrix=None,
                      stream=None):
-        """Queues a search; `out` must be device memory (e.g. a CUDA tensor)."""
-        q, ql, nq = _query_args(queries, q_lengths)
+        """Queues a search; `out` must be device memory (e.g. a CUDA tensor).
+        The queries and lengths are read on the host before this returns."""
+        q, ql, nq = _query_args(_host(queries, "uint8"), _host(q_lengths, "int32"))
+        out = _scores_out(out, nq, self.db.n)
         m = _matrix(matrix)
         self._keep = (q, ql, m, out)
         _check(lib().sw_plan_search_async(self._h, _ptr(q), _ptr(ql), nq, gap_open, gap_extend,
@@ -355,10 +397,21 @@ def search_pairs_noalloc(queries, q_offsets, q_lengths, subjects, s_offsets, s_l
     """sw_search_pairs_noalloc: all pairs, for callers that cannot let the
     library allocate.  Every array is caller-owned CUDA memory (torch CUDA
     tensors) except `matrix` (host); subjects are at most 4096 residues."""
-    m = _matrix(matrix)
+    want = {"queries": (queries, "uint8"), "q_offsets": (q_offsets, "int64"),
+            "q_lengths": (q_lengths, "int32"), "subjects": (subjects, "uint8"),
+            "s_offsets": (s_offsets, "int64"), "s_lengths": (s_lengths, "int32"),
+            "scores": (scores, "int32")}
+    for name, (x, dtype) in want.items():
+        if not (hasattr(x, "data_ptr") and x.is_cuda and str(x.dtype) == "torch." + dtype):
+            raise TypeError(f"{name} must be a {dtype} torch tensor on the GPU")
+    nq, ns = int(q_lengths.shape[0]), int(s_lengths.shape[0])
+    if q_offsets.shape[0] != nq or s_offsets.shape[0] != ns:
+        raise ValueError("one offset per sequence")
+    scores = _scores_out(scores, nq, ns)
+    m = None if matrix is None else _host(_matrix(matrix), "int8")   # host memory
     _check(lib().sw_search_pairs_noalloc(
-        _ptr(queries), _ptr(q_offsets), _ptr(q_lengths), int(q_lengths.shape[0]),
-        _ptr(subjects), _ptr(s_offsets), _ptr(s_lengths), int(s_lengths.shape[0]),
+        _ptr(queries), _ptr(q_offsets), _ptr(q_lengths), nq,
+        _ptr(subjects), _ptr(s_offsets), _ptr(s_lengths), ns,
         gap_open, gap_extend, _ptr(m), _ptr(scores), _stream(stream)))
     return scores
 
