@@ -9,7 +9,8 @@ row against every subject.
 * Admission: every request needs device memory for its scores row
   (4 bytes x subjects) and its share of the plan's query/flag buffers; a
   request is admitted while the bytes of all admitted, unfinished requests
-  stay within ``memory_budget``.  A request that could never fit is refused
+  stay within ``memory_budget`` (by default the bytes the slots hold, so
+  only an explicit, smaller budget holds requests back).  A request that could never fit is refused
   at once (``AdmissionError``), never queued forever.
 * Continuous batching: a scheduler thread takes the admitted requests that
   have arrived, up to ``max_batch`` queries and ``max_batch_residues``
@@ -58,8 +59,14 @@ class Request:
 
 
 class _Slot:
+    """One batch in flight: a plan, a CUDA stream and a device scores buffer.
+
+    The scheduler talks to a slot only through ``launch``, ``poll``,
+    ``rows`` and ``close`` (and ``bind_thread`` once, on its own thread)."""
+
     def __init__(self, db, max_batch, max_residues, opts):
         import torch
+        self.device = db.device
         self.plan = db.plan(max_batch, max_residues, **opts)
         self.stream = torch.cuda.Stream(device=db.device)
         self.scores = torch.empty((max_batch, db.n), dtype=torch.int32,
@@ -71,22 +78,47 @@ class _Slot:
     def busy(self) -> bool:
         return bool(self.requests)
 
+    def bind_thread(self):
+        import torch
+        torch.cuda.set_device(self.device)
+
+    def launch(self, queries, lengths, gap_open, gap_extend, matrix):
+        """Queues the batch's search on the slot's stream."""
+        self.plan.search_async(queries, lengths, self.scores[:lengths.size], gap_open,
+                               gap_extend, matrix, stream=self.stream)
+
+    def poll(self) -> bool:
+        """True once the batch's scores are complete (raises if it failed)."""
+        return self.plan.wait(0)
+
+    def rows(self, n) -> np.ndarray:
+        """The finished batch's first n score rows, on the host."""
+        return self.scores[:n].cpu().numpy()
+
+    def close(self):
+        self.plan.close()
+
 
 class Server:
     """Continuous-batching search server over one resident Database."""
 
     def __init__(self, db: swgb.Database, slots: int = 2, max_batch: int = 16,
                  max_batch_residues: int = 65536, memory_budget: int | None = None,
-                 gap_open: int = 10, gap_extend: int = 2, matrix=None, **plan_opts):
+                 gap_open: int = 10, gap_extend: int = 2, matrix=None, slot_factory=None,
+                 **plan_opts):
+        """``slot_factory(db, max_batch, max_batch_residues, plan_opts)`` makes
+        one slot (default: a plan, a stream and a scores buffer on the GPU)."""
         self.db = db
         self.max_batch = int(max_batch)
         self.max_batch_residues = int(max_batch_residues)
         self.gap_open, self.gap_extend, self.matrix = gap_open, gap_extend, matrix
-        self.slots = [_Slot(db, self.max_batch, self.max_batch_residues, plan_opts)
+        make = slot_factory or _Slot
+        self.slots = [make(db, self.max_batch, self.max_batch_residues, plan_opts)
                       for _ in range(int(slots))]
-        per_row = 4 * db.n
+        # default: what the slots hold, every slot's batch full (max_batch
+        # requests' score rows and flag shares, max_batch_residues residues)
         self.memory_budget = int(memory_budget) if memory_budget else \
-            len(self.slots) * self.max_batch * per_row * 2
+            len(self.slots) * (self.max_batch * self.request_bytes(0) + self.max_batch_residues)
         self._lock = threading.Condition()
         self._pending: collections.deque[Request] = collections.deque()
         self._in_use = 0
@@ -142,7 +174,6 @@ class Server:
     def _launch(self, slot: _Slot, batch: list[Request]):
         q = np.concatenate([r.query for r in batch]) if batch else np.zeros(0, np.uint8)
         lens = np.array([r.query.size for r in batch], dtype=np.int32)
-        out = slot.scores[:len(batch)]
         now = time.perf_counter()
         for r in batch:
             r.started = now
@@ -150,13 +181,12 @@ class Server:
         slot.batch_id = self._batches
         self._batches += 1
         slot.requests = batch
-        slot.plan.search_async(q, lens, out, self.gap_open, self.gap_extend, self.matrix,
-                               stream=slot.stream)
+        slot.launch(q, lens, self.gap_open, self.gap_extend, self.matrix)
         self.max_concurrent = max(self.max_concurrent, sum(s.busy for s in self.slots))
 
     def _complete(self, slot: _Slot):
         batch = slot.requests
-        rows = slot.scores[:len(batch)].cpu().numpy()  # the slot's stream has finished
+        rows = slot.rows(len(batch))  # the slot's stream has finished
         now = time.perf_counter()
         with self._lock:
             for i, r in enumerate(batch):
@@ -169,14 +199,14 @@ class Server:
             r.future.set_result(rows[i].copy())
 
     def _loop(self):
-        import torch
-        torch.cuda.set_device(self.db.device)
+        if self.slots:
+            self.slots[0].bind_thread()
         while True:
             progressed = False
             for s in self.slots:
                 if s.busy:
                     try:
-                        done = s.plan.wait(0)
+                        done = s.poll()
                     except Exception as e:  # a failed batch fails its requests only
                         for r in s.requests:
                             r.future.set_exception(e)
@@ -215,7 +245,7 @@ class Server:
             self._lock.notify_all()
         self._thread.join(timeout)
         for s in self.slots:
-            s.plan.close()
+            s.close()
 
     # ---- reporting --------------------------------------------------------------
     def report(self, wall_s: float | None = None) -> dict:
