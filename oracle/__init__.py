@@ -10,7 +10,7 @@ What it follows (arxiv 2309.09609):
     score = the largest H (scalar int32 C in ``sw_oracle.c``).
   * Section IV-A: BLOSUM62 scoring, gap penalties "10/2".
 
-Readings of the paper taken here (each is listed in the design doc):
+Readings of the paper taken here, where it is silent or open to two readings:
   * Gap convention: the library's ``(gap_open, gap_extend)`` means a gap of k
     residues costs ``gap_open + k * gap_extend``.  In the notation of Eq. 2-3
     that is ``Go = gap_open + gap_extend`` and ``Ge = gap_extend``.  The
