@@ -94,6 +94,14 @@ def parse():
     return ap.parse_args()
 
 
+def workload_config(w) -> dict:
+    """The keys that name a workload in both arms' config."""
+    return {"workload": w.name, "queries": len(w.queries), "subjects": len(w.db),
+            "query_residues": w.queries.total, "db_residues": w.db.total, "cells": w.cells,
+            "gaps": [w.gap_open, w.gap_extend], "matrix": "BLOSUM62",
+            "planted_homologs": int(w.planted.size)}
+
+
 def make_workload(name, seed, subjects=None, queries=None, query_offset=0):
     from paper_2309_09609_gb300 import synth
     kw = {}
@@ -226,8 +234,9 @@ def run_reference(args):
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
            "data": "synthetic",
-           "config": {"workload": w.name, "sample": f"all {len(w.queries)} queries x first "
-                      f"{len(sub)} subjects ({cells:.3e} cells per step)"},
+           "config": {**workload_config(w), "parallelism": f"{cores} host threads",
+                      "sample": f"all {len(w.queries)} queries x first {len(sub)} subjects "
+                      f"({cells:.3e} cells per step)"},
            "cpu_baseline": {"value": round(g, 4), "unit": "GCUPS", "cores": cores,
                             "kind": "oracle", "sample": f"{len(sub)} subjects x all queries"},
            "e2e": {"value": round(g, 4), "unit": "GCUPS", "h2d_bytes_per_step": 0,
@@ -425,10 +434,7 @@ def run_native(args):
               "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
               "dtype": "i16x2+i32", "data": "synthetic",
-              "config": {"workload": w.name, "queries": nq, "subjects": N,
-                         "query_residues": q.total, "db_residues": db.total, "cells": cells,
-                         "gaps": [w.gap_open, w.gap_extend], "matrix": "BLOSUM62",
-                         "planted_homologs": int(w.planted.size),
+              "config": {**workload_config(w),
                          "l2": "no flush: device-resident DB layouts (~2x DB residues bytes) > 129 MB L2",
                          "parallelism": f"replicas{world}" if world > 1 else "1 GPU",
                          "plan": {k: getattr(swgb.options(**opts), k) for k, _ in swgb.Options._fields_}},

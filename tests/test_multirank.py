@@ -68,4 +68,9 @@ def test_reference_arm_runs_on_rank_zero_only():
     line = json.loads(outs[0][0].strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+    # the same workload keys as the GPU arm's config
+    import bench
+    w = bench.make_workload("plain-small", 0)
+    cfg = line["config"]
+    assert {k: cfg[k] for k in bench.workload_config(w)} == bench.workload_config(w)
     assert outs[1][0].strip() == ""
