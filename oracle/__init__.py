@@ -87,9 +87,11 @@ def _ptr(a: np.ndarray):
 
 
 def encode(text: str) -> np.ndarray:
-    """Letters -> codes 0..23 in ALPHABET order; unknown letters -> X."""
+    """One code per character: letters -> codes 0..23 in ALPHABET order (a-z
+    folded to A-Z, nothing else), anything else -> X."""
     table = {c: i for i, c in enumerate(ALPHABET)}
-    return np.array([table.get(c, CODE_X) for c in text.upper()], dtype=np.uint8)
+    fold = {chr(c): chr(c - 32) for c in range(ord("a"), ord("z") + 1)}
+    return np.array([table.get(fold.get(c, c), CODE_X) for c in text], dtype=np.uint8)
 
 
 def blosum62() -> np.ndarray:

@@ -46,6 +46,11 @@ def test_default_matrix_equals_oracle_table(lib):
 def test_encode_matches_oracle(lib):
     text = "ARNDCQEGHILKMFPSTWYVBZX*uojarnd?!. "
     assert (swgb.encode(text) == oracle.encode(text)).all()
+    # every byte value, including those above 127
+    every = bytes(range(256)).decode("latin-1")
+    got = swgb.encode(every)
+    assert (got == oracle.encode(every)).all() and got.max() < 24
+    assert swgb.encode("").size == 0
 
 
 def test_options_default(lib):
