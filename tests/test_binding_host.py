@@ -76,3 +76,76 @@ def test_noalloc_wants_gpu_tensors_of_the_stated_types():
         swgb.search_pairs_noalloc(q, off, ln, q, off, ln, sc)       # host tensors
     with pytest.raises(TypeError, match="queries"):
         swgb.search_pairs_noalloc(q.numpy(), off, ln, q, off, ln, sc)   # numpy
+
+
+class FakeLib:
+    """Stands in for libswgb.so: records every call, returns SW_OK.  Handles
+    it creates stay NULL, so closing them is a no-op with any library."""
+
+    def __init__(self):
+        self.calls = []
+
+    def __getattr__(self, name):
+        def call(*args):
+            self.calls.append((name, args))
+            return 0
+        return call
+
+    def last(self, name):
+        return [a for n, a in self.calls if n == name][-1]
+
+
+@pytest.fixture
+def fake(monkeypatch):
+    f = FakeLib()
+    f.sw_last_error = lambda: b""
+    monkeypatch.setattr(swgb, "_lib", f)
+    return f
+
+
+def test_wrappers_pass_counts_and_buffers_of_the_stated_types(fake):
+    db = swgb.Database(np.array([1, 2, 3, 4, 5], np.uint8), [2, 3])
+    assert db.n == 2 and db.subject_lengths().tolist() == [2, 3]
+    res, lens, n, dev, _ = fake.last("sw_db_create")
+    assert n == 2 and dev == 0
+    out = db.search([4, 5, 6], torch.tensor([1, 2], dtype=torch.int64), 10, 2)
+    assert out.shape == (2, 2) and out.dtype == np.int32
+    h, q, ql, nq, go, ge, m, sc, st = fake.last("sw_search")
+    assert nq == 2 and (go, ge) == (10, 2) and m is None and st is None
+    plan = db.plan(4, 100, rows_per_thread=16)
+    o = fake.last("sw_plan_create")[3]._obj
+    assert o.rows_per_thread == 16
+    buf = np.zeros((1, 2), np.int32)
+    assert plan.search(np.array([7], np.uint8), [1], out=buf) is buf
+    with pytest.raises(ValueError):
+        plan.search(np.array([7], np.uint8), [1], out=np.zeros((2, 2), np.int32))
+    dev_out = torch.zeros((1, 2), dtype=torch.int32)
+    plan.search_async(torch.tensor([7], dtype=torch.uint8), [1], dev_out)
+    assert fake.last("sw_plan_search_async")[3] == 1
+    assert plan.wait(0) is True and isinstance(plan.stats(), dict)
+
+
+def test_align_sizes_the_transcript_buffer_and_checks_indices(fake):
+    db = swgb.Database(np.arange(10, dtype=np.uint8) % 20, [4, 6])
+    q, ql = np.arange(7, dtype=np.uint8), np.array([3, 4], np.int32)
+    got = db.align(q, ql, [0, 1, 1], [1, 0, 1])
+    assert len(got) == 3 and all(g["ops"] == "" for g in got)
+    args = fake.last("sw_align")
+    n_pairs, ops_capacity = args[6], args[12]
+    assert n_pairs == 3 and ops_capacity == (3 + 6) + (4 + 4) + (4 + 6)
+    for pq, ps in [([2], [0]), ([-1], [0]), ([0], [2]), ([0], [-1])]:
+        with pytest.raises(swgb.SwError) as e:
+            db.align(q, ql, pq, ps)
+        assert e.value.status == swgb.SW_EINVAL
+    with pytest.raises(ValueError):
+        db.align(q, ql, [0, 1], [0])
+    assert db.align(q, ql, [], []) == []
+
+
+def test_a_failing_call_raises_with_the_library_message(fake, monkeypatch):
+    monkeypatch.setattr(fake, "sw_last_error", lambda: b"queries is NULL", raising=False)
+    fake.sw_search = lambda *a: swgb.SW_EINVAL
+    db = swgb.Database(np.array([1], np.uint8), [1])
+    with pytest.raises(swgb.SwError, match="SW_EINVAL: queries is NULL") as e:
+        db.search([1], [1])
+    assert e.value.status == swgb.SW_EINVAL
