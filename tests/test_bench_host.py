@@ -50,3 +50,9 @@ def test_oracle_sample_fits_the_cell_budget():
             if len(sub) < len(w.db):          # one more subject would not fit
                 assert cells + int(w.queries.total) * int(w.db.lens[len(sub)]) > budget
             assert (sub.lens == w.db.lens[:len(sub)]).all()
+
+
+def test_l2_note_follows_the_database_size():
+    import bench
+    assert "> 129 MB L2" in bench.l2_note(205_430_861)        # the paper-shaped database
+    assert "fit in L2" in bench.l2_note(1_070_512)            # the small parity case
