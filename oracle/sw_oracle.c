@@ -138,7 +138,7 @@ static void *worker(void *arg) {
       if ((int64_t)n + 1 > cap) {
         free(buf);
         cap = 2 * ((int64_t)n + 1);
-        buf = (int32_t *)malloc(sizeof(int32_t) * 2 * cap);
+        buf = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)cap);
         if (!buf) { jb->failed = 1; return NULL; }
       }
       jb->out[k] = gotoh(jb->qres + jb->qoff[qi], m, jb->dres + jb->doff[di], n,
