@@ -1,6 +1,7 @@
-"""The N > 1 host path of bench.py on CPU: two gloo ranks, barrier and the
-max-over-ranks timing reduction (each rank runs an independent replica; the
-search itself has no collective)."""
+"""The N > 1 host path of bench.py on CPU: two gloo ranks, barrier, the
+max-over-ranks timing reduction and the sum of the cells the ranks scored
+(each rank runs its own seeded search of the same shape; the search itself
+has no collective)."""
 import os
 import socket
 import subprocess
@@ -28,13 +29,23 @@ CHILD = textwrap.dedent("""
     dist.barrier()
     t = bench.max_over_ranks(10.0 + rank, dist, "cpu")
     assert t == 11.0, t
+    c = bench.sum_over_ranks(1e12 * (1 + rank), dist, "cpu")
+    assert c == 3e12, c
+    # each rank its own search of the same shape; rank 0 = the one-GPU workload
+    import argparse
+    a = argparse.Namespace(workload="plain-small", seed=0, subjects=None, queries=None,
+                           query_offset=0)
+    w = bench.rank_workload(a, rank)
+    w0 = bench.make_workload("plain-small", 0)
+    assert len(w.db) == len(w0.db) and len(w.queries) == len(w0.queries)
+    assert (w.db.res.size == w0.db.res.size and (w.db.res == w0.db.res).all()) == (rank == 0)
     dist.barrier()
     dist.destroy_process_group()
     print("ok", rank)
 """)
 
 
-def test_two_gloo_ranks_reduce_max_time():
+def test_two_gloo_ranks_reduce_time_and_cells():
     port = _free_port()
     procs = []
     for rank in range(2):
