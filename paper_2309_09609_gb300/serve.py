@@ -24,6 +24,10 @@ row against every subject.
   p99 185 ms, against 101 ms and 274 ms with 4 slots.
 * Completion is observed per slot; each request gets its scores, its
   latency (arrival to completion on the host) and the batch it rode in.
+* Cancellation: ``submit`` returns a ``concurrent.futures.Future``.
+  Cancelling it before its batch is launched drops the request, which is then
+  never admitted or searched.  Once launched it is running and can no longer
+  be cancelled, as for any Future.
 """
 from __future__ import annotations
 
@@ -125,6 +129,7 @@ class Server:
         self._next_id = 0
         self._batches = 0
         self.max_concurrent = 0       # most batches in flight at once
+        self.cancelled = 0            # requests cancelled before they were launched
         self._stop = False
         self.completed: list[Request] = []
         self._thread = threading.Thread(target=self._loop, daemon=True)
@@ -155,16 +160,25 @@ class Server:
 
     # ---- scheduler ---------------------------------------------------------------
     def _take_batch(self):
-        """Admitted requests for one batch (called with the lock held)."""
+        """Admitted requests for one batch (called with the lock held).  A
+        request cancelled while it waited is dropped here; the ones taken are
+        marked running, so from then on they can no longer be cancelled."""
         batch, residues = [], 0
         while self._pending and len(batch) < self.max_batch:
             r = self._pending[0]
+            if r.future.cancelled():
+                self._pending.popleft()
+                self.cancelled += 1
+                continue
             need = self.request_bytes(r.query.size)
             if residues + r.query.size > self.max_batch_residues:
                 break
             if self._in_use + need > self.memory_budget:
                 break
             self._pending.popleft()
+            if not r.future.set_running_or_notify_cancel():   # cancelled just now
+                self.cancelled += 1
+                continue
             self._in_use += need
             r.admitted = time.perf_counter()
             batch.append(r)
@@ -257,7 +271,7 @@ class Server:
                 "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
                 "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
                 "mean_batch": len(self.completed) / max(self._batches, 1),
-                "max_concurrent_batches": self.max_concurrent,
+                "max_concurrent_batches": self.max_concurrent, "cancelled": self.cancelled,
                 "gcups": cells / wall_s / 1e9 if wall_s else None, "wall_s": wall_s}
 
 

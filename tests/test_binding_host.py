@@ -149,3 +149,20 @@ def test_a_failing_call_raises_with_the_library_message(fake, monkeypatch):
     with pytest.raises(swgb.SwError, match="SW_EINVAL: queries is NULL") as e:
         db.search([1], [1])
     assert e.value.status == swgb.SW_EINVAL
+
+
+def test_a_closed_database_is_refused_by_the_library():
+    # the real libswgb: a closed handle is NULL, which every entry point
+    # rejects with SW_EINVAL before any CUDA call
+    from paper_2309_09609_gb300 import build as nvbuild
+    nvbuild.build()
+    swgb.lib()
+    db = object.__new__(swgb.Database)
+    db._h, db.n, db.device, db._lens = None, 2, 0, np.array([3, 4], np.int32)
+    for call in (lambda: db.search([1, 2], [2]),
+                 lambda: db.search_plain([1, 2], [2]),
+                 lambda: db.plan(1, 2),
+                 lambda: db.align(np.array([1, 2], np.uint8), [2], [0], [1])):
+        with pytest.raises(swgb.SwError) as e:
+            call()
+        assert e.value.status == swgb.SW_EINVAL and "NULL" in str(e.value)

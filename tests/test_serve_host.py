@@ -235,3 +235,27 @@ def test_replay_submits_a_trace_in_time_order():
     assert all(a.arrival <= b.arrival for a, b in zip(arr, arr[1:]))
     rep = srv.report()
     assert rep["requests"] == 30 and rep["p50_ms"] <= rep["p99_ms"]
+
+
+def test_cancelled_requests_are_dropped_before_launch_and_running_ones_finish():
+    gate = Gate()
+    srv = server(gate, slots=1, max_batch=1)
+    try:
+        futs = [srv.submit(q) for q in queries([11, 12, 13, 14])]
+        deadline = time.time() + 10
+        while not FakeSlot.log and time.time() < deadline:
+            time.sleep(0.001)
+        assert FakeSlot.log == [[11]]
+        assert futs[0].cancel() is False            # launched: running, not cancellable
+        assert futs[2].cancel() is True             # still queued
+        gate.event.set()
+        assert futs[0].result(10).shape == (N_SUBJECTS,)
+        assert futs[1].result(10).shape == (N_SUBJECTS,)
+        assert futs[3].result(10).shape == (N_SUBJECTS,)
+        assert futs[2].cancelled()
+    finally:
+        gate.event.set()
+        srv.close(timeout=10)
+    assert [lens for lens in FakeSlot.log] == [[11], [12], [14]]   # 13 never searched
+    rep = srv.report()
+    assert rep["cancelled"] == 1 and rep["requests"] == 3 and srv._in_use == 0
