@@ -16,6 +16,7 @@
 #include <chrono>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <numeric>
@@ -115,6 +116,16 @@ extern "C" void sw_options_default(sw_options* opt) {
 }
 
 // ---- small helpers ----------------------------------------------------------------
+// Host-side fault injection for tests: with SWGB_FAULT=alloc the device
+// allocations of sw_db_create and sw_plan_create report out-of-memory, and
+// with SWGB_FAULT=copy the first copy of a search reports a failed copy, so
+// the error paths run without a device fault.  Read at every call; unset, it
+// changes nothing.
+static bool injected_fault(const char* what) {
+  const char* f = getenv("SWGB_FAULT");
+  return f && strcmp(f, what) == 0;
+}
+
 static bool is_device_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes a;
@@ -259,7 +270,7 @@ extern "C" sw_status sw_db_create(const uint8_t* residues, const int32_t* length
   sw_db* db = new sw_db();
   db->device = device;
   db->residues = total;
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = injected_fault("alloc") ? cudaErrorMemoryAllocation : cudaSuccess;
 #define DB_ALLOC_COPY(dst, src, count)                                                     \
   if (e == cudaSuccess) e = dalloc(&db->dst, (count));                                     \
   if (e == cudaSuccess && (count) > 0)                                                     \
@@ -545,7 +556,7 @@ extern "C" sw_status sw_plan_create(sw_db* db, int32_t max_queries, int64_t max_
   const int64_t WP = (int64_t)(p->pair_blocks16 + p->pair_blocks32) * PAIR_WARPS;
   p->scr.pair_rows16 = (int64_t)p->pair_blocks16 * PAIR_WARPS;
 
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = injected_fault("alloc") ? cudaErrorMemoryAllocation : cudaSuccess;
   const int64_t nres = std::max<int64_t>(max_query_residues, 1);
   p->scr.inter_stride_vec = (int64_t)(L_inter / CHUNK) * 4 * 32;
   p->scr.intra_stride = std::max(v.max_len, 1);
@@ -735,6 +746,8 @@ static sw_status plan_enqueue(sw_plan* p, const HostBatch& hb, int32_t nq, int32
   memcpy(p->qlen_h, hb.len.data(), sizeof(int32_t) * nq);
   memcpy(p->qorder_h, hb.order.data(), sizeof(int32_t) * nq);
   if (hb.total > 0) memcpy(p->qres_h, hb.res, (size_t)hb.total);
+  if (injected_fault("copy"))
+    return sw_set_cuda_error(cudaErrorInvalidValue, "query upload (injected fault)");
   CUDA_TRY(cudaMemcpyAsync(p->qres, p->qres_h, (size_t)std::max<int64_t>(hb.total, 1), cudaMemcpyHostToDevice, s));
   if (nq > 0) {
     CUDA_TRY(cudaMemcpyAsync(p->qoff, p->qoff_h, sizeof(int64_t) * nq, cudaMemcpyHostToDevice, s));
