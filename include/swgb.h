@@ -28,6 +28,10 @@
  *     detects which.  Inputs are borrowed for the duration of the call only.
  *   - Every call returns a status; on failure sw_last_error() describes it.
  *     No call aborts the process, traps on the device or waits unboundedly.
+ *   - Testing hook: with the environment variable SWGB_FAULT=alloc the device
+ *     allocations of sw_db_create and sw_plan_create fail with SW_ENOMEM, and
+ *     with SWGB_FAULT=copy a search's first copy fails with SW_ECUDA (read at
+ *     every call; unset in normal use).
  */
 #ifndef SWGB_H
 #define SWGB_H
