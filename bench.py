@@ -111,6 +111,20 @@ def l2_note(db_residues: int) -> str:
             f"parity-size case, not a bandwidth claim")
 
 
+def paper_arch_efficiency(gcups_per_gpu, i32_rate, sms, mhz) -> dict:
+    """The paper's architectural efficiency (Section II-C, Eq. 4-5): achieved
+    GCUPS over the peak of Algorithm 1's 12 int32 instructions per cell at
+    the measured int32 max rate (lane-ops per SM clock x SMs x clock; one
+    ALU-pipe instruction, which the algorithm's six max operations need).
+    The packed path does two cells per 5.5 ALU ops, so it can exceed 1."""
+    from paper_2309_09609_gb300 import perfmodel
+    peak = perfmodel.theoretical_peak_gcups(sms, 1, i32_rate, mhz)
+    return {"value": round(perfmodel.arch_efficiency(gcups_per_gpu, peak), 4),
+            "peak_gcups": round(peak, 1),
+            "model": f"Eq. 5: imax {i32_rate:.1f} lane-ops/clk/SM x {sms} SMs x {mhz:.0f} MHz "
+                     f"/ {perfmodel.PAPER_INSTRUCTIONS_PER_CELL} instructions per cell"}
+
+
 def workload_config(w) -> dict:
     """The keys that name a workload in both arms' config."""
     return {"workload": w.name, "queries": len(w.queries), "subjects": len(w.db),
@@ -517,6 +531,9 @@ def run_native(args):
                           "peak_gcups": round(peak * 1e12 / PACKED_ALU_OPS_PER_CELL / 1e9, 1),
                           "pair_kernel_ms": per_kernel["pair_kernel (packed intra-task)"]["ms"],
                           "recompute_ms": round(statistics.mean(recompute_ms), 3)}
+
+    i32_rate, _, _ = swgb.intpeak("imax", 8, 256, 20000)
+    result["paper_arch_efficiency"] = paper_arch_efficiency(gcups / world, i32_rate, sms, max_mhz)
 
     # plain int32 one-query-per-launch baseline on the same workload
     if not args.no_plain:

@@ -56,3 +56,12 @@ def test_l2_note_follows_the_database_size():
     import bench
     assert "> 129 MB L2" in bench.l2_note(205_430_861)        # the paper-shaped database
     assert "fit in L2" in bench.l2_note(1_070_512)            # the small parity case
+
+
+def test_paper_arch_efficiency_follows_eq5():
+    import bench
+    # Eq. 4-5 by hand: 46 SMs x 64 lane-ops per clock x 1725 MHz / 12 per cell
+    r = bench.paper_arch_efficiency(280.2, 64.0, 46, 1725.0)
+    assert abs(r["peak_gcups"] - 46 * 64 * 1725e6 / 12 / 1e9) < 0.1
+    assert abs(r["value"] - 280.2 / (46 * 64 * 1725e6 / 12 / 1e9)) < 1e-4
+    assert bench.paper_arch_efficiency(5965.0, 62.5, 152, 2070.0)["value"] > 1   # packed
