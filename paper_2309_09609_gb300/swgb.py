@@ -392,6 +392,21 @@ class Plan:
         return s.as_dict()
 
 
+def top_hits(scores, k: int):
+    """Each query's k best subjects from a score matrix [queries, subjects]
+    (numpy or torch, host or device): (subject indices, scores), both
+    [queries, min(k, subjects)], best first, ties in subject order.  The
+    indices feed ``Database.align`` directly, e.g. with
+    ``np.repeat(np.arange(nq), k)`` and ``idx.ravel()``."""
+    s = scores.cpu().numpy() if hasattr(scores, "cpu") else np.asarray(scores)
+    if s.ndim != 2:
+        raise ValueError("scores must be [queries, subjects]")
+    k = max(0, min(int(k), s.shape[1]))
+    # a stable sort on the negated scores keeps equal scores in subject order
+    idx = np.argsort(-s.astype(np.int64), axis=1, kind="stable")[:, :k]
+    return idx.astype(np.int64), np.take_along_axis(s, idx, axis=1)
+
+
 def search_pairs_noalloc(queries, q_offsets, q_lengths, subjects, s_offsets, s_lengths, scores,
                          gap_open=10, gap_extend=2, matrix=None, stream=None):
     """sw_search_pairs_noalloc: all pairs, for callers that cannot let the

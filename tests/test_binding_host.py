@@ -166,3 +166,15 @@ def test_a_closed_database_is_refused_by_the_library():
         with pytest.raises(swgb.SwError) as e:
             call()
         assert e.value.status == swgb.SW_EINVAL and "NULL" in str(e.value)
+
+
+def test_top_hits_orders_by_score_then_subject():
+    s = np.array([[5, 9, 9, 0, 7], [0, 0, 0, 0, 0], [1, 2, 3, 4, 5]], np.int32)
+    idx, val = swgb.top_hits(s, 3)
+    assert idx.tolist() == [[1, 2, 4], [0, 1, 2], [4, 3, 2]]
+    assert val.tolist() == [[9, 9, 7], [0, 0, 0], [5, 4, 3]]
+    idx, val = swgb.top_hits(torch.from_numpy(s), 10)      # k larger than the subjects
+    assert idx.shape == (3, 5) and val[0].tolist() == [9, 9, 7, 5, 0]
+    assert swgb.top_hits(s, 0)[0].shape == (3, 0)
+    with pytest.raises(ValueError):
+        swgb.top_hits(s[0], 2)
