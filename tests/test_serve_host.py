@@ -158,7 +158,8 @@ def test_the_default_budget_admits_every_slot_full():
     gate = Gate()
     srv = server(gate, slots=2, max_batch=3, max_batch_residues=30)
     try:
-        futs = [srv.submit(q) for q in queries([10] * 7)]
+        with srv._lock:     # all seven queued before the scheduler looks (the lock is reentrant)
+            futs = [srv.submit(q) for q in queries([10] * 7)]
         deadline = time.time() + 10
         while sum(len(b) for b in FakeSlot.log) < 6 and time.time() < deadline:
             time.sleep(0.001)
