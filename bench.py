@@ -81,7 +81,7 @@ def parse():
                     help="shrink the database (profiling / small cases)")
     ap.add_argument("--queries", type=int, default=None, help="keep only N queries")
     ap.add_argument("--query-offset", type=int, default=0, help="first query kept by --queries")
-    ap.add_argument("--serve", type=int, default=200,
+    ap.add_argument("--serve", type=int, default=1000,
                     help="serving leg: arrivals replayed against the resident DB (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=50.0, help="Poisson arrival rate (1/s)")
     ap.add_argument("--serve-slots", type=int, default=2,
@@ -95,6 +95,10 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-align", action="store_true", help="skip the traceback leg")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the batched-uneven and long-sequence records of the default run")
+    ap.add_argument("--config-steps", type=int, default=2,
+                    help="timed steps of each further workload record (about 6-9 s each)")
     return ap.parse_args()
 
 
@@ -401,6 +405,200 @@ def run_align(d, q, db, scores, w):
             "equals_oracle": bool(same)}
 
 
+def timed_steps(plan, q_dev, l_dev, out, w, steps, warmup, stream, local, dist):
+    """W untimed warm-up searches, then exactly `steps` timed ones between a
+    barrier and synchronize on both sides, with CUDA events on the plan's
+    stream and nvidia-smi clocks sampled meanwhile."""
+    import torch
+
+    def step():
+        plan.search(q_dev, l_dev, w.gap_open, w.gap_extend, None, out=out, stream=stream)
+
+    for _ in range(max(warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    kernel_ms, recompute_ms, pair_ms = [], [], []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        evs[0].record(stream)
+        for i in range(steps):
+            step()
+            evs[i + 1].record(stream)
+            st = plan.stats()
+            kernel_ms.append(st["search_ms"])
+            recompute_ms.append(st["recompute_ms"])
+            pair_ms.append(st["pair_ms"])
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    return {"step_ms": [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)],
+            "total_ms": evs[0].elapsed_time(evs[-1]), "kernel_ms": kernel_ms,
+            "recompute_ms": recompute_ms, "pair_ms": pair_ms, "stats": plan.stats(),
+            "clocks": clk.summary()}
+
+
+def roofline(t, peak, peak_source, rate_mhz, traffic):
+    """The integer roofline of the dominant kernel of a timed search: ALU-pipe
+    lane-ops vs the intpeak microbenchmark's measured DPX throughput (SMs x
+    clock x per-SM rate).  The inter-task kernel scores the short subjects'
+    cells, the packed pair kernel the rest (subjects longer than the cutoff);
+    both run the same packed recurrence, so both count the same lane-ops per
+    cell."""
+    stats = t["stats"]
+    per_kernel = {}
+    for name, kcells, kms_list in (
+            ("inter_kernel (packed inter-task)", stats["inter_cells"], t["kernel_ms"]),
+            ("pair_kernel (packed intra-task)", stats["cells"] - stats["inter_cells"], t["pair_ms"])):
+        kms = statistics.mean(kms_list) if kms_list else float("nan")
+        ach = PACKED_ALU_OPS_PER_CELL * kcells / (kms / 1e3) / 1e12 if kcells else 0.0
+        per_kernel[name] = {"ms": round(kms, 3), "cells": int(kcells), "achieved": round(ach, 3),
+                            "frac": round(ach / peak, 4)}
+    dominant = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
+    dom = per_kernel[dominant]
+    inter = dominant.startswith("inter_kernel")
+    return {"bound": "alu", "achieved": dom["achieved"], "peak": round(peak, 3),
+            "unit": "Tops/s", "frac": dom["frac"],
+            "traffic": traffic("inter_kernel" if inter else "pair_kernel"),
+            "kernel": dominant, "kernel_ms": dom["ms"], "kernel_cells": dom["cells"],
+            "kernels": per_kernel,
+            "alu_ops_per_cell": PACKED_ALU_OPS_PER_CELL,
+            "peak_source": peak_source,
+            "intpeak_clock_mhz": round(rate_mhz, 1),
+            "peak_gcups": round(peak * 1e12 / PACKED_ALU_OPS_PER_CELL / 1e9, 1),
+            "pair_kernel_ms": per_kernel["pair_kernel (packed intra-task)"]["ms"],
+            "recompute_ms": round(statistics.mean(t["recompute_ms"]), 3)}
+
+
+def cpu_leg(w, got_host, budget):
+    """The CPU oracle on all queries x the first subjects that fit `budget`
+    cells, on every host core: the baseline, and parity of those pairs."""
+    import oracle
+    oracle.build()
+    sub = oracle_sample(w, budget)
+    cores = os.cpu_count() or 1
+    ref, ocells, odt = time_oracle(w, sub, cores)
+    got = np.asarray(got_host)[:, :len(sub)]
+    return ({"value": round(ocells / odt / 1e9, 4), "unit": "GCUPS", "cores": cores,
+             "kind": "oracle",
+             "sample": f"all {len(w.queries)} queries x first {len(sub)} subjects "
+                       f"({ocells:.3e} cells, {odt:.1f} s)"},
+            bool((got == ref).all()))
+
+
+def plain_leg(d, q, w, device, stream, rows=None):
+    """The plain int32 one-query-per-launch baseline (sw_search_plain) on the
+    queries `rows` (default all), timed with CUDA events; and its scores."""
+    import torch
+    sub = q if rows is None else q.subset(rows)
+    qd = torch.from_numpy(sub.res).to(device)
+    ld = torch.from_numpy(sub.lens).to(device)
+    outp = torch.empty((len(sub), d.n), dtype=torch.int32, device=device)
+    d.search_plain(qd, ld, w.gap_open, w.gap_extend, out=outp, stream=stream)  # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    d.search_plain(qd, ld, w.gap_open, w.gap_extend, out=outp, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    pms = e0.elapsed_time(e1)
+    cells = sub.total * w.db.total
+    return {"value": round(cells / (pms / 1e3) / 1e9, 2), "unit": "GCUPS", "ms": round(pms, 3),
+            "launches": len(sub)}, outp
+
+
+def e2e_leg(plan, q, N, w, repeats, dist, device):
+    """The search through the C ABI with host (pinned) buffers, the query
+    upload and the score download inside the timed region."""
+    import torch
+    q_host = torch.from_numpy(q.res).pin_memory()
+    l_host = torch.from_numpy(q.lens).pin_memory()
+    out_host = torch.empty((len(q), N), dtype=torch.int32).pin_memory()
+    plan.search(q_host, l_host, w.gap_open, w.gap_extend, None, out=out_host)
+    e2e = []
+    for _ in range(max(1, repeats)):
+        t0 = time.perf_counter()
+        plan.search(q_host, l_host, w.gap_open, w.gap_extend, None, out=out_host)
+        e2e.append(time.perf_counter() - t0)
+    return max_over_ranks(statistics.mean(e2e), dist, device), out_host
+
+
+def run_config(name, args, device, local, stream, peak, peak_src, rate_mhz):
+    """A further workload measured in the same run (one GPU): its own timed
+    steps, roofline, plain-baseline speed-up, e2e, CPU baseline and parity
+    on the CPU sample."""
+    import torch
+    from paper_2309_09609_gb300 import swgb
+    w = make_workload(name, args.seed)
+    q, db = w.queries, w.db
+    d = swgb.Database.from_seqset(db, device=local)
+    opts, tuned = {}, None
+    if name == "batched-uneven":    # the autotuned plan, replayed from one graph
+        from paper_2309_09609_gb300 import tune
+        t0 = time.perf_counter()
+        tr = tune.tune(d, q, w.gap_open, w.gap_extend, cache=None)
+        opts = dict(tr["options"], use_graph=1)
+        tuned = {"options": tr["options"], "candidates": len(tr["timings"]),
+                 "seconds": round(time.perf_counter() - t0, 2)}
+    plan = d.plan(len(q), q.total, **opts)
+    q_dev = torch.from_numpy(q.res).to(device)
+    l_dev = torch.from_numpy(q.lens).to(device)
+    out = torch.empty((len(q), len(db)), dtype=torch.int32, device=device)
+    steps = args.config_steps
+    t = timed_steps(plan, q_dev, l_dev, out, w, steps, args.warmup, stream, local, None)
+    ms = t["total_ms"] / steps
+    rec = {"workload": workload_config(w), "value": round(w.cells / (ms / 1e3) / 1e9, 2),
+           "unit": "GCUPS", "steps": steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+           "latency_ms": {"p50": round(float(np.percentile(t["step_ms"], 50)), 3),
+                          "p99": round(float(np.percentile(t["step_ms"], 99)), 3)},
+           "l2": l2_note(db.total), "recomputed_pairs": t["stats"]["recomputed_pairs"],
+           "gpu_launches": t["stats"]["kernels_launched"] * steps,
+           "plan": {k: getattr(swgb.options(**opts), k) for k, _ in swgb.Options._fields_},
+           "autotuned": tuned, "clocks": t["clocks"]}
+    sub_args = argparse.Namespace(**{**vars(args), "workload": name, "tune": name == "batched-uneven"})
+    rec["roofline"] = roofline(t, peak, peak_src, rate_mhz, lambda k: profiled_traffic(sub_args, k))
+    # plain int32 baseline: one launch per query, so its rate per query does
+    # not depend on how many queries run; timed on a stated sample
+    if name == "batched-uneven":
+        rows = np.arange(0, len(q), 20)
+        pl, outp = plain_leg(d, q, w, device, stream, rows)
+        pl["sample"] = f"{rows.size} of {len(q)} queries (every 20th), all subjects"
+        rec["plain_int32"] = pl
+        rec["plain_equals_packed"] = bool(torch.equal(outp, out[torch.from_numpy(rows).to(device)]))
+    else:
+        # long subjects: the plain kernel gives each subject one thread, so a
+        # launch lasts as long as its longest pair (about 9 M cells/s per
+        # thread: minutes per query here).  Timed on the shortest query
+        # against the first 2,000 subjects of at most 8,000 residues.
+        qi = int(np.argmin(q.lens))
+        idx = np.nonzero(db.lens <= 8000)[0][:2000]
+        small = db.subset(idx)
+        ds = swgb.Database.from_seqset(small, device=local)
+        ws = argparse.Namespace(db=small, gap_open=w.gap_open, gap_extend=w.gap_extend)
+        pl, outp = plain_leg(ds, q, ws, device, stream, [qi])
+        pl["sample"] = (f"the shortest query ({int(q.lens[qi])} residues) x the first {idx.size} "
+                        f"subjects of at most 8,000 residues")
+        rec["plain_int32"] = pl
+        sel = torch.from_numpy(idx).to(device)
+        rec["plain_equals_packed"] = bool(torch.equal(outp[0], out[qi].index_select(0, sel)))
+        del ds
+    rec["speedup_vs_plain"] = round(rec["value"] / pl["value"], 3)
+    e2e_s, out_host = e2e_leg(plan, q, len(db), w, 1, None, device)
+    rec["e2e"] = {"value": round(w.cells / e2e_s / 1e9, 2), "unit": "GCUPS",
+                  "h2d_bytes_per_step": int(q.total + 4 * len(q)),
+                  "d2h_bytes_per_step": int(4 * len(q) * len(db)),
+                  "ms_per_step": round(1e3 * e2e_s, 3)}
+    if not args.no_cpu:
+        rec["cpu_baseline"], rec["parity_on_cpu_sample"] = cpu_leg(
+            w, out_host.numpy(), CPU_CELLS[name])
+    plan.close()
+    d.close()
+    return rec
+
+
 def run_native(args):
     import torch
     rank, world, local, dist = dist_setup(args)
@@ -446,41 +644,15 @@ def run_native(args):
     l_dev = torch.from_numpy(q.lens).to(device)
     out = torch.empty((nq, N), dtype=torch.int32, device=device)
 
-    def step():
-        plan.search(q_dev, l_dev, w.gap_open, w.gap_extend, None, out=out, stream=stream)
-
-    for _ in range(max(args.warmup, 1)):
-        step()
-    torch.cuda.synchronize()
-
     # timed region: device-resident inputs (the DB layouts, ~2 x residues bytes,
     # exceed the 129 MB L2, so no flush is needed between steps)
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    kernel_ms, recompute_ms, pair_ms = [], [], []
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        evs[0].record(stream)
-        for i in range(args.steps):
-            step()
-            evs[i + 1].record(stream)
-            st = plan.stats()
-            kernel_ms.append(st["search_ms"])
-            recompute_ms.append(st["recompute_ms"])
-            pair_ms.append(st["pair_ms"])
-        torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
-    total_ms = evs[0].elapsed_time(evs[-1])
-    total_ms = max_over_ranks(total_ms, dist, device)
+    t = timed_steps(plan, q_dev, l_dev, out, w, args.steps, args.warmup, stream, local, dist)
+    total_ms = max_over_ranks(t["total_ms"], dist, device)
     ms = total_ms / args.steps
     all_cells = sum_over_ranks(float(cells), dist, device)   # each rank its own search
     gcups = all_cells / (ms / 1e3) / 1e9
-    stats = plan.stats()
-    clocks = clk.summary()
+    stats = t["stats"]
+    clocks = t["clocks"]
 
     result = {"metric": METRIC, "value": round(gcups, 2), "unit": "GCUPS", "n_gpus": world,
               "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
@@ -491,78 +663,35 @@ def run_native(args):
                          "parallelism": (f"{world} GPUs, one independent search each "
                                          f"(seed + rank)") if world > 1 else "1 GPU",
                          "plan": {k: getattr(swgb.options(**opts), k) for k, _ in swgb.Options._fields_}},
-              "latency_ms": {"p50": round(float(np.percentile(step_ms, 50)), 3),
-                             "p99": round(float(np.percentile(step_ms, 99)), 3)},
+              "latency_ms": {"p50": round(float(np.percentile(t["step_ms"], 50)), 3),
+                             "p99": round(float(np.percentile(t["step_ms"], 99)), 3)},
               "recomputed_pairs": stats["recomputed_pairs"],
               "autotuned": tuned,
               "db_create_s": round(db_create_s, 3),
               "gpu_launches": stats["kernels_launched"] * args.steps,
               "clocks": clocks}
 
-    # roofline of the dominant kernel: ALU-pipe lane-ops vs the intpeak
-    # microbenchmark's measured DPX throughput (SMs x clock x per-SM rate).
-    # The inter-task kernel scores the short subjects' cells, the packed pair
-    # kernel the rest (subjects longer than the cutoff); both run the same
-    # packed recurrence, so both count the same lane-ops per cell.
     sms = torch.cuda.get_device_properties(device).multi_processor_count
     rate, rate_mhz, _ = swgb.intpeak("viaddmax_s16x2", 8, 256, 20000)
     max_mhz = clocks.get("sm_max_mhz") or 2070.0
     peak = rate * sms * max_mhz * 1e6 / 1e12
-    per_kernel = {}
-    for name, kcells, kms_list in (
-            ("inter_kernel (packed inter-task)", stats["inter_cells"], kernel_ms),
-            ("pair_kernel (packed intra-task)", stats["cells"] - stats["inter_cells"], pair_ms)):
-        kms = statistics.mean(kms_list) if kms_list else float("nan")
-        ach = PACKED_ALU_OPS_PER_CELL * kcells / (kms / 1e3) / 1e12 if kcells else 0.0
-        per_kernel[name] = {"ms": round(kms, 3), "cells": int(kcells), "achieved": round(ach, 3),
-                            "frac": round(ach / peak, 4)}
-    dominant = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
-    dom = per_kernel[dominant]
-    inter = dominant.startswith("inter_kernel")
-    result["roofline"] = {"bound": "alu", "achieved": dom["achieved"], "peak": round(peak, 3),
-                          "unit": "Tops/s", "frac": dom["frac"],
-                          "traffic": profiled_traffic(args, "inter_kernel" if inter else "pair_kernel"),
-                          "kernel": dominant, "kernel_ms": dom["ms"], "kernel_cells": dom["cells"],
-                          "kernels": per_kernel,
-                          "alu_ops_per_cell": PACKED_ALU_OPS_PER_CELL,
-                          "peak_source": f"intpeak viaddmax_s16x2 {rate:.1f} lane-ops/clk/SM x "
-                                         f"{sms} SMs x {max_mhz:.0f} MHz (max SM clock), measured",
-                          "intpeak_clock_mhz": round(rate_mhz, 1),
-                          "peak_gcups": round(peak * 1e12 / PACKED_ALU_OPS_PER_CELL / 1e9, 1),
-                          "pair_kernel_ms": per_kernel["pair_kernel (packed intra-task)"]["ms"],
-                          "recompute_ms": round(statistics.mean(recompute_ms), 3)}
+    peak_src = (f"intpeak viaddmax_s16x2 {rate:.1f} lane-ops/clk/SM x {sms} SMs x "
+                f"{max_mhz:.0f} MHz (max SM clock), measured")
+    result["roofline"] = roofline(t, peak, peak_src, rate_mhz, lambda k: profiled_traffic(args, k))
 
     i32_rate, _, _ = swgb.intpeak("imax", 8, 256, 20000)
     result["paper_arch_efficiency"] = paper_arch_efficiency(gcups / world, i32_rate, sms, max_mhz)
 
     # plain int32 one-query-per-launch baseline on the same workload
     if not args.no_plain:
-        outp = torch.empty_like(out)
-        d.search_plain(q_dev, l_dev, w.gap_open, w.gap_extend, out=outp, stream=stream)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        d.search_plain(q_dev, l_dev, w.gap_open, w.gap_extend, out=outp, stream=stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        pms = e0.elapsed_time(e1)
-        pg = cells / (pms / 1e3) / 1e9
-        result["plain_int32"] = {"value": round(pg, 2), "unit": "GCUPS", "ms": round(pms, 3),
-                                 "launches": nq}
-        result["speedup_vs_plain"] = round(cells / (ms / 1e3) / 1e9 / pg, 3)   # this rank
+        pl, outp = plain_leg(d, q, w, device, stream)
+        result["plain_int32"] = pl
+        result["speedup_vs_plain"] = round(cells / (ms / 1e3) / 1e9 / pl["value"], 3)   # this rank
         result["plain_equals_packed"] = bool(torch.equal(outp, out))
+        del outp
 
     # end to end through the C ABI with host buffers (pinned), copies timed
-    q_host = torch.from_numpy(q.res).pin_memory()
-    l_host = torch.from_numpy(q.lens).pin_memory()
-    out_host = torch.empty((nq, N), dtype=torch.int32).pin_memory()
-    plan.search(q_host, l_host, w.gap_open, w.gap_extend, None, out=out_host)
-    e2e = []
-    for _ in range(max(1, min(args.steps, 3))):
-        t0 = time.perf_counter()
-        plan.search(q_host, l_host, w.gap_open, w.gap_extend, None, out=out_host)
-        e2e.append(time.perf_counter() - t0)
-    e2e_s = max_over_ranks(statistics.mean(e2e), dist, device)
+    e2e_s, out_host = e2e_leg(plan, q, N, w, min(args.steps, 3), dist, device)
     result["e2e"] = {"value": round(all_cells / e2e_s / 1e9, 2), "unit": "GCUPS",
                      "h2d_bytes_per_step": int(q.total + 4 * nq),
                      "d2h_bytes_per_step": int(4 * nq * N), "ms_per_step": round(1e3 * e2e_s, 3)}
@@ -577,17 +706,21 @@ def run_native(args):
 
     # CPU oracle on a bounded sample (rank 0, N = 1): baseline and parity check
     if rank == 0 and world == 1 and not args.no_cpu:
-        import oracle
-        oracle.build()
-        sub = oracle_sample(w, args.cpu_cells or CPU_CELLS[args.workload])
-        cores = os.cpu_count() or 1
-        ref, ocells, odt = time_oracle(w, sub, cores)
-        got = out_host.numpy()[:, :len(sub)]
-        result["cpu_baseline"] = {"value": round(ocells / odt / 1e9, 4), "unit": "GCUPS",
-                                  "cores": cores, "kind": "oracle",
-                                  "sample": f"all {nq} queries x first {len(sub)} subjects "
-                                            f"({ocells:.3e} cells, {odt:.1f} s)"}
-        result["parity_on_cpu_sample"] = bool((got == ref).all())
+        result["cpu_baseline"], result["parity_on_cpu_sample"] = cpu_leg(
+            w, out_host.numpy(), args.cpu_cells or CPU_CELLS[args.workload])
+
+    # the batched-uneven and long-sequence workloads, each measured in full
+    # in the same run (one GPU, the default workload only)
+    if (rank == 0 and world == 1 and args.workload == "paper-search" and not args.no_configs
+            and not args.subjects and not args.queries):
+        del out, out_host, plan
+        d.close()
+        torch.cuda.empty_cache()
+        result["configs"] = {}
+        for name in ("batched-uneven", "long"):
+            result["configs"][name.replace("-", "_")] = run_config(
+                name, args, device, local, stream, peak, peak_src, rate_mhz)
+            torch.cuda.empty_cache()
     if rank == 0:
         print(json.dumps(result), flush=True)
     if dist:

@@ -47,7 +47,8 @@ typedef enum {
   SW_EINVAL = 1,     /* bad argument: residue code >= 24, negative length, NULL ... */
   SW_ENOMEM = 2,     /* device or host allocation failed */
   SW_ECUDA = 3,      /* a CUDA runtime call failed */
-  SW_ETIMEDOUT = 4,  /* a bounded device-side wait gave up */
+  SW_ETIMEDOUT = 4,  /* sw_plan_wait: the search is still running when its host-side
+                        time limit is up (no kernel of the library waits on the device) */
   SW_EBUSY = 5       /* the plan's capacity is exceeded or it is in use */
 } sw_status;
 
@@ -119,6 +120,11 @@ typedef struct {
                                 instead of after them, so its blocks take the SMs that their
                                 tails leave (lower latency for small searches); search_ms and
                                 pair_ms then overlap, both from the start; default 0 */
+  int32_t flag_capacity;     /* entries of the plan's list of saturated pairs (8 bytes each);
+                                0: min(max_queries x subjects, 2^20).  More saturated pairs
+                                than this in one search are still scored exactly, in further
+                                rounds of the int32 kernel after the search (see
+                                sw_stats.overflow_rounds) */
 } sw_options;
 
 void sw_options_default(sw_options* opt);
@@ -129,7 +135,9 @@ typedef struct {
   int64_t inter_items;       /* (query, group of 64 subjects) work items */
   int64_t intra_items;       /* (query, long subject) work items */
   int64_t recomputed_pairs;  /* pairs whose 16-bit score saturated, redone in int32 */
-  int32_t timed_out;         /* 1 if a bounded device wait gave up */
+  int32_t overflow_rounds;   /* extra rounds of the int32 kernel that the last search ran
+                                because it had more saturated pairs than the plan's flag list
+                                holds (0 normally); their time is not in recompute_ms */
   int32_t kernels_launched;  /* kernels of this library launched by the search */
   float search_ms;           /* device time of the inter-task search kernel (CUDA events) */
   float recompute_ms;        /* device time of the int32 intra-task kernel (CUDA events):
@@ -142,9 +150,15 @@ typedef struct {
 } sw_stats;
 
 /* Creates a search context for up to max_queries queries holding up to
- * max_query_residues residues in total, on the database's device.  All
- * device memory the search needs (query buffer, border scratch, saturation
- * list, work counters) is allocated here, once.  opt may be NULL.
+ * max_query_residues residues in total, on the database's device.  The
+ * device memory a search needs is allocated here, once: the query buffers,
+ * the per-warp border scratch of each kernel (a fixed amount for the device
+ * and database, about 2.2 GB on a GB300 for a database whose longest subject
+ * has 35,000 residues, independent of the queries), the saturated-pair list
+ * (opt.flag_capacity entries of 8 bytes, 8 MiB by default) and the work
+ * counters.  One more buffer, max_queries x subjects int32, is allocated by
+ * the first search whose scores go to host memory, and kept.  opt may be
+ * NULL.
  * Errors: SW_EINVAL, SW_ENOMEM, SW_ECUDA. */
 sw_status sw_plan_create(sw_db* db, int32_t max_queries, int64_t max_query_residues,
                          const sw_options* opt, sw_plan** out);
@@ -171,7 +185,7 @@ void sw_plan_destroy(sw_plan* plan);
  * The call returns after the scores are in `scores` (it synchronises the
  * stream).  One plan serves one call at a time (SW_EBUSY otherwise).
  * Errors: SW_EINVAL (bad code, length, gap or size), SW_EBUSY (capacity),
- * SW_ECUDA, SW_ETIMEDOUT. */
+ * SW_ECUDA. */
 sw_status sw_plan_search(sw_plan* plan, const uint8_t* queries, const int32_t* q_lengths,
                          int32_t n_queries, int32_t gap_open, int32_t gap_extend,
                          const int8_t* matrix, int32_t* scores, void* stream);
@@ -192,8 +206,12 @@ sw_status sw_plan_wait(sw_plan* plan, int32_t timeout_ms);
 /* Statistics of the plan's last completed search. */
 sw_status sw_plan_stats(const sw_plan* plan, sw_stats* out);
 
-/* One-shot exact search: creates a plan sized for this call, runs
- * sw_plan_search and frees it.  Same arguments and errors as sw_plan_search. */
+/* One-shot exact search: sw_plan_search through a plan that the database
+ * keeps for these calls.  The first call creates it (default options, sized
+ * for its batch), later calls reuse it, and a batch larger than it holds
+ * replaces it with one sized for both; it is freed by sw_db_destroy.  Calls
+ * on one database are serialized (they would share the GPU anyway).  Same
+ * arguments and errors as sw_plan_search. */
 sw_status sw_search(sw_db* db, const uint8_t* queries, const int32_t* q_lengths,
                     int32_t n_queries, int32_t gap_open, int32_t gap_extend,
                     const int8_t* matrix, int32_t* scores, void* stream);
@@ -250,13 +268,17 @@ sw_status sw_align(sw_db* db, const uint8_t* queries, const int32_t* q_lengths, 
  * of memory.  Every other search entry point allocates (a database, a plan,
  * kernel scratch); this one calls no cudaMalloc, cudaFree or other allocating
  * routine.
- *   queries, subjects:     concatenated residue codes, device memory.
+ *   queries, subjects:     concatenated residue codes, device memory of the
+ *                          current device; may be NULL when every length on
+ *                          that side is 0.
  *   q_offsets, s_offsets:  int64 start of each sequence, device memory.
  *   q_lengths, s_lengths:  int32 lengths, device memory; subjects may be at
  *                          most 4096 residues long, queries any length.
  *   matrix:                24 x 24 int8 SM(query, subject), HOST memory
  *                          (NULL = BLOSUM62).
  *   scores:                n_queries x n_subjects int32, device memory.
+ * Every device buffer must belong to the current device (or be managed
+ * memory); the call checks this before any launch.
  * Same gap convention and the same scores as sw_search.  The kernel's
  * scratch (one border row per warp, a work counter, a status word) is a
  * file-scope device array of ~16 MiB that every GPU loading the library holds
@@ -266,9 +288,12 @@ sw_status sw_align(sw_db* db, const uint8_t* queries, const int32_t* q_lengths, 
  * stream capture.  All calls share the one array, so calls whose work
  * overlaps on the GPU (other streams, other threads) race: serialize them.
  * The call returns after the scores are written (it synchronizes the stream).
- * Errors: SW_EINVAL for negative counts or gaps, a NULL buffer, a negative
- * length, a subject longer than 4096 residues or a code >= 24 (such pairs are
- * not scored); SW_ECUDA. */
+ * Errors: SW_EINVAL for negative counts or gaps, a NULL buffer, a buffer
+ * that is not memory of the current device, a negative length, a subject
+ * longer than 4096 residues, a NULL residue buffer with a positive length, or
+ * a code >= 24.  Pairs with a bad length or code are not scored: their
+ * entries of `scores` keep what they held; every other pair is scored.
+ * SW_ECUDA. */
 sw_status sw_search_pairs_noalloc(const uint8_t* queries, const int64_t* q_offsets,
                                   const int32_t* q_lengths, int32_t n_queries,
                                   const uint8_t* subjects, const int64_t* s_offsets,

@@ -113,6 +113,7 @@ extern "C" void sw_options_default(sw_options* opt) {
   opt->wide_min_subject = 4096;
   opt->inter_columns = 8;
   opt->overlap_kernels = 0;
+  opt->flag_capacity = 0;
 }
 
 // ---- small helpers ----------------------------------------------------------------
@@ -170,6 +171,8 @@ static void parallel_for(int64_t n, F f) {
 }
 
 // ---- database -----------------------------------------------------------------------
+static void plan_free(sw_plan* p);
+
 struct sw_db {
   int device = 0;
   DbView view{};
@@ -186,10 +189,14 @@ struct sw_db {
   int64_t* coff = nullptr;
   int32_t* clen = nullptr;
   int32_t* perm = nullptr;
+  // the plan behind sw_search, kept between calls (guarded by oneshot_mu)
+  sw_plan* oneshot = nullptr;
+  std::mutex oneshot_mu;
 };
 
 static void db_free(sw_db* db) {
   if (!db) return;
+  plan_free(db->oneshot);
   int cur = 0;
   cudaGetDevice(&cur);
   cudaSetDevice(db->device);
@@ -416,7 +423,9 @@ struct sw_plan {
   int64_t* qoff = nullptr;
   int32_t* qlen = nullptr;
   int32_t* qorder = nullptr;
-  int32_t* scores_dev = nullptr;  // used when the caller's scores live on the host
+  int32_t* scores_dev = nullptr;  // used when the caller's scores live on the host:
+                                  // allocated by the first such search
+  cudaStream_t stream = nullptr;  // the stream of the search in flight
   SearchParams* params = nullptr;
   SearchState* state = nullptr;
   Scratch scr{};
@@ -500,6 +509,7 @@ extern "C" sw_status sw_plan_create(sw_db* db, int32_t max_queries, int64_t max_
     return sw_set_error(SW_EINVAL, "inter_columns must be 4 or 8");
   if (o.wide_min_len < 0 || o.wide_min_subject < 0)
     return sw_set_error(SW_EINVAL, "wide_min_len and wide_min_subject must be >= 0");
+  if (o.flag_capacity < 0) return sw_set_error(SW_EINVAL, "flag_capacity < 0");
   CUDA_TRY(cudaSetDevice(db->device));
 
   sw_plan* p = new sw_plan();
@@ -561,13 +571,15 @@ extern "C" sw_status sw_plan_create(sw_db* db, int32_t max_queries, int64_t max_
   p->scr.inter_stride_vec = (int64_t)(L_inter / CHUNK) * 4 * 32;
   p->scr.intra_stride = std::max(v.max_len, 1);
   p->scr.pair_stride = std::max(v.max_len, 1);
-  p->scr.flag_capacity = (int64_t)max_queries * std::max<int64_t>(v.n, 1);
+  p->scr.flag_capacity = o.flag_capacity > 0
+                            ? (int64_t)o.flag_capacity
+                            : std::min<int64_t>((int64_t)max_queries * std::max<int64_t>(v.n, 1),
+                                                DEFAULT_FLAG_CAPACITY);
   if (e == cudaSuccess) e = dalloc(&p->scr.pair_border, (size_t)(WP * p->scr.pair_stride));
   if (e == cudaSuccess) e = dalloc(&p->qres, nres);
   if (e == cudaSuccess) e = dalloc(&p->qoff, max_queries);
   if (e == cudaSuccess) e = dalloc(&p->qlen, max_queries);
   if (e == cudaSuccess) e = dalloc(&p->qorder, 2 * (size_t)max_queries);  // qorder, then qpair
-  if (e == cudaSuccess) e = dalloc(&p->scores_dev, (size_t)max_queries * std::max<int64_t>(v.n, 1));
   if (e == cudaSuccess) e = dalloc(&p->params, 1);
   if (e == cudaSuccess) e = dalloc(&p->state, 1);
   if (e == cudaSuccess) e = dalloc(&p->scr.inter_border, (size_t)(W * std::max<int64_t>(p->scr.inter_stride_vec, 1)));
@@ -755,6 +767,7 @@ static sw_status plan_enqueue(sw_plan* p, const HostBatch& hb, int32_t nq, int32
     CUDA_TRY(cudaMemcpyAsync(p->qorder, p->qorder_h, sizeof(int32_t) * 2 * nq, cudaMemcpyHostToDevice, s));
   }
   CUDA_TRY(cudaMemcpyAsync(p->params, p->params_h, sizeof(SearchParams), cudaMemcpyHostToDevice, s));
+  p->stream = s;
   CUDA_TRY(run_kernels(p, s));
   CUDA_TRY(cudaMemcpyAsync(p->state_h, p->state, sizeof(SearchState), cudaMemcpyDeviceToHost, s));
   p->pending = sw_stats{};
@@ -778,9 +791,42 @@ static void finish_stats(sw_plan* p) {
     cudaGetLastError();
     p->stats.pair_ms = p->stats.search_ms = p->stats.recompute_ms = -1.f;
   }
-  p->stats.recomputed_pairs = (int64_t)std::min<unsigned long long>(
-      p->state_h->n_flags, (unsigned long long)p->scr.flag_capacity);
+  p->stats.recomputed_pairs = (int64_t)p->state_h->n_flags;
   p->in_flight = false;
+}
+
+// More saturated pairs than the flag list holds: the packed kernels wrote
+// FLAG_SENTINEL for those that found it full.  Each round collects the
+// marked pairs into the list (counting all of them) and recomputes the
+// listed ones in int32, whose exact scores replace the marks; the round in
+// which every marked pair fits the list is the last.  Runs after the search
+// has completed, synchronously on its stream.
+static cudaError_t overflow_rounds(sw_plan* p, int32_t* rounds) {
+  *rounds = 0;
+  cudaStream_t s = p->stream;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->db->device);
+  unsigned long long nf = p->state_h->n_flags;
+  while (nf > (unsigned long long)p->scr.flag_capacity) {
+    cudaError_t e = cudaMemsetAsync(p->state, 0, sizeof(SearchState), s);
+    if (e == cudaSuccess) e = launch_collect(4 * std::max(sms, 1), p->db->view, p->params, p->state, p->scr, s);
+    if (e == cudaSuccess) e = launch_intra(p->ikc, p->db->view, p->params, p->state, p->scr, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(p->state_h, p->state, sizeof(SearchState), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    nf = p->state_h->n_flags;
+    ++*rounds;
+  }
+  return cudaSuccess;
+}
+
+// Statistics, then any overflow rounds, of a search that has completed.
+static sw_status complete_search(sw_plan* p) {
+  finish_stats(p);
+  cudaError_t e = overflow_rounds(p, &p->stats.overflow_rounds);
+  if (e != cudaSuccess) return sw_set_cuda_error(e, "recompute of the flag-list overflow");
+  return SW_OK;
 }
 
 extern "C" sw_status sw_plan_search(sw_plan* plan, const uint8_t* queries, const int32_t* q_lengths,
@@ -797,17 +843,37 @@ extern "C" sw_status sw_plan_search(sw_plan* plan, const uint8_t* queries, const
   if (n_queries > 0 && N > 0 && !scores) return sw_set_error(SW_EINVAL, "scores is NULL");
   cudaStream_t s = (cudaStream_t)stream;
   const bool dev_out = is_device_ptr(scores);
+  if (!dev_out && !plan->scores_dev) {
+    // scores for a host buffer are staged on the device: the first such
+    // search allocates the plan's staging buffer
+    cudaError_t ea = injected_fault("alloc") ? cudaErrorMemoryAllocation
+                                             : dalloc(&plan->scores_dev,
+                                                      (size_t)plan->max_queries * std::max<int64_t>(N, 1));
+    if (ea != cudaSuccess) {
+      plan->scores_dev = nullptr;
+      return sw_set_cuda_error(ea, "sw_plan_search: host-order scores buffer");
+    }
+  }
   int32_t* target = dev_out ? scores : plan->scores_dev;
   st = plan_enqueue(plan, hb, n_queries, gap_open, gap_extend, matrix, target, s);
   if (st != SW_OK) return st;
   plan->in_flight = true;
-  if (!dev_out && n_queries > 0 && N > 0)
-    CUDA_TRY(cudaMemcpyAsync(scores, plan->scores_dev, sizeof(int32_t) * (size_t)n_queries * N,
-                             cudaMemcpyDeviceToHost, s));
+  const size_t out_bytes = sizeof(int32_t) * (size_t)n_queries * (size_t)N;
+  if (!dev_out && out_bytes > 0)
+    CUDA_TRY(cudaMemcpyAsync(scores, plan->scores_dev, out_bytes, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaEventRecord(plan->done, s));
   cudaError_t e = cudaEventSynchronize(plan->done);
-  finish_stats(plan);
-  if (e != cudaSuccess) return sw_set_cuda_error(e, "sw_plan_search");
+  if (e != cudaSuccess) {
+    finish_stats(plan);
+    return sw_set_cuda_error(e, "sw_plan_search");
+  }
+  st = complete_search(plan);
+  if (st != SW_OK) return st;
+  if (plan->stats.overflow_rounds > 0 && !dev_out && out_bytes > 0) {
+    // the copy above predates the overflow rounds' scores
+    CUDA_TRY(cudaMemcpyAsync(scores, plan->scores_dev, out_bytes, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+  }
   CUDA_TRY(cudaGetLastError());
   return SW_OK;
 }
@@ -839,10 +905,7 @@ extern "C" sw_status sw_plan_wait(sw_plan* plan, int32_t timeout_ms) {
   const auto t0 = std::chrono::steady_clock::now();
   for (;;) {
     cudaError_t e = cudaEventQuery(plan->done);
-    if (e == cudaSuccess) {
-      finish_stats(plan);
-      return SW_OK;
-    }
+    if (e == cudaSuccess) return complete_search(plan);
     if (e != cudaErrorNotReady) {
       plan->in_flight = false;
       return sw_set_cuda_error(e, "sw_plan_wait");
@@ -866,19 +929,31 @@ extern "C" sw_status sw_search(sw_db* db, const uint8_t* queries, const int32_t*
                                const int8_t* matrix, int32_t* scores, void* stream) {
   sw_clear_error();
   if (!db) return sw_set_error(SW_EINVAL, "db is NULL");
+  CUDA_TRY(cudaSetDevice(db->device));
   HostBatch hb;
   sw_status st = read_batch(queries, q_lengths, n_queries, hb);
   if (st != SW_OK) return st;
-  sw_plan* plan = nullptr;
-  sw_options o;
-  sw_options_default(&o);
-  o.use_graph = 0;
-  st = sw_plan_create(db, std::max(n_queries, 1), hb.total, &o, &plan);
-  if (st != SW_OK) return st;
-  st = sw_plan_search(plan, queries, q_lengths, n_queries, gap_open, gap_extend, matrix, scores,
-                      stream);
-  sw_plan_destroy(plan);
-  return st;
+  std::lock_guard<std::mutex> guard(db->oneshot_mu);
+  sw_plan*& plan = db->oneshot;
+  int32_t want_q = std::max(n_queries, 1);
+  int64_t want_res = hb.total;
+  if (plan && (plan->max_queries < want_q || plan->max_residues < want_res)) {
+    want_q = std::max(want_q, plan->max_queries);
+    want_res = std::max(want_res, plan->max_residues);
+    plan_free(plan);
+    plan = nullptr;
+  }
+  if (!plan) {
+    sw_options o;
+    sw_options_default(&o);
+    st = sw_plan_create(db, want_q, want_res, &o, &plan);
+    if (st != SW_OK) {
+      plan = nullptr;
+      return st;
+    }
+  }
+  return sw_plan_search(plan, queries, q_lengths, n_queries, gap_open, gap_extend, matrix, scores,
+                        stream);
 }
 
 // ---- plain baseline ----------------------------------------------------------------------

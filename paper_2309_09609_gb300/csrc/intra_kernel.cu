@@ -255,6 +255,30 @@ intra_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scr
   }
 }
 
+// Pairs marked FLAG_SENTINEL by a packed kernel whose flag list was full:
+// each (query, sorted subject) slot is read once, grid-stride, and every
+// marked pair is counted and, while there is room, listed.
+__global__ void collect_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st,
+                               Scratch scr) {
+  const int64_t slots = (int64_t)db.groups * GROUP;
+  const int64_t total = (int64_t)P->nq * slots;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(i / slots);
+    const int s = (int)(i - (int64_t)q * slots);
+    const int orig = db.perm[s];
+    if (orig < 0 || P->scores[(int64_t)q * db.n + orig] != FLAG_SENTINEL) continue;
+    const unsigned long long k = atomicAdd(&st->n_flags, 1ull);
+    if ((int64_t)k < scr.flag_capacity) scr.flags[k] = make_int2(q, s);
+  }
+}
+
+cudaError_t launch_collect(int blocks, const DbView& db, const SearchParams* params,
+                           SearchState* state, const Scratch& scr, cudaStream_t stream) {
+  collect_kernel<<<blocks, 256, 0, stream>>>(db, params, state, scr);
+  return cudaGetLastError();
+}
+
 typedef void (*IntraKernel)(DbView, const SearchParams*, SearchState*, Scratch);
 
 static IntraKernel pick_intra(int rows) {

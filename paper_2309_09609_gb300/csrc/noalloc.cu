@@ -71,14 +71,17 @@ noalloc_kernel(const uint8_t* __restrict__ qres, const int64_t* __restrict__ qof
     if ((long long)it >= total) break;
     const int q = (int)((long long)it / ns), s = (int)((long long)it % ns);
     const int m = qlen[q], n = slen[s];
-    if (m < 0 || n < 0 || n > NA_MAX_LEN) {  // rejected: nothing is read or written
+    // rejected, with nothing read or written: a negative length, a subject
+    // over the limit, or residues to read from a NULL buffer
+    if (m < 0 || n < 0 || n > NA_MAX_LEN || (m > 0 && !qres) || (n > 0 && !sres)) {
       if (lane == 0) atomicOr(status, NA_BAD_LENGTH);
       continue;
     }
-    const uint8_t* qr = qres + qoff[q];
-    const uint8_t* d = sres + soff[s];
+    const uint8_t* qr = qres + (m > 0 ? qoff[q] : 0);
+    const uint8_t* d = sres + (n > 0 ? soff[s] : 0);
     const int npass = (m + ROWS - 1) / ROWS;
     int S = 0;
+    int bad = 0;  // this lane met a residue code >= 24: the pair gets no score
     for (int p = 0; p < npass && n > 0; p++) {
       __syncwarp();
       const int i0 = p * ROWS + lane * NA_TI;
@@ -88,6 +91,7 @@ noalloc_kernel(const uint8_t* __restrict__ qres, const int64_t* __restrict__ qof
         int c = (i0 + r < m) ? (int)qr[i0 + r] : -1;
         if (c >= ALPHA) {
           atomicOr(status, NA_BAD_CODE);
+          bad = 1;
           c = -1;
         }
         qc[r] = c;
@@ -129,7 +133,8 @@ noalloc_kernel(const uint8_t* __restrict__ qres, const int64_t* __restrict__ qof
           int c = d[j];
           if (c >= ALPHA) {
             atomicOr(status, NA_BAD_CODE);
-            c = PAD_CODE;
+            bad = 1;
+            c = PAD_CODE;  // keeps the profile read in bounds; the score is dropped
           }
           const uint2 pw = *(const uint2*)(prof + (c * 32 + lane) * NA_TI);
           int hd = hdiag;
@@ -155,8 +160,21 @@ noalloc_kernel(const uint8_t* __restrict__ qres, const int64_t* __restrict__ qof
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) S = max(S, __shfl_xor_sync(NA_FULL, S, o));
+    if (__any_sync(NA_FULL, bad)) continue;  // warp-uniform: the pair is not scored
     if (lane == 0) scores[(long long)q * ns + s] = S;
   }
+}
+
+// True when p is device memory of device `dev` (or managed memory), which a
+// kernel launched on `dev` may read and write.
+bool on_device(const void* p, int dev) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 std::mutex g_na_lock;
@@ -197,8 +215,21 @@ extern "C" sw_status sw_search_pairs_noalloc(const uint8_t* queries, const int64
   if (gap_open < 0 || gap_extend < 0 || gap_open > 100000000 || gap_extend > 100000000)
     return sw_set_error(SW_EINVAL, "sw_search_pairs_noalloc: gap penalties must be in [0, 1e8]");
   if (n_queries == 0 || n_subjects == 0) return SW_OK;
-  if (!queries || !q_offsets || !q_lengths || !subjects || !s_offsets || !s_lengths || !scores)
+  // the residue buffers may be NULL when every length on that side is 0
+  // (the kernel refuses to read a NULL buffer); the others are always read
+  if (!q_offsets || !q_lengths || !s_offsets || !s_lengths || !scores)
     return sw_set_error(SW_EINVAL, "sw_search_pairs_noalloc: NULL buffer");
+  int cur = 0;
+  CUDA_TRY(cudaGetDevice(&cur));
+  const void* bufs[7] = {queries, q_offsets, q_lengths, subjects, s_offsets, s_lengths, scores};
+  static const char* names[7] = {"queries", "q_offsets", "q_lengths", "subjects",
+                                 "s_offsets", "s_lengths", "scores"};
+  for (int i = 0; i < 7; i++) {
+    if (!bufs[i]) continue;
+    if (!on_device(bufs[i], cur))
+      return sw_set_error(SW_EINVAL, "sw_search_pairs_noalloc: %s is not device memory of the "
+                          "current device (%d)", names[i], cur);
+  }
   NaMatrix mat;
   int8_t m[ALPHA * ALPHA];
   if (matrix)

@@ -298,7 +298,10 @@ pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scra
       if (orig >= 0) {
         if (sb >= P->sat_threshold) {
           const unsigned long long k = atomicAdd(&st->n_flags, 1ull);
-          if ((int64_t)k < scr.flag_capacity) scr.flags[k] = make_int2(q, sidx);
+          if ((int64_t)k < scr.flag_capacity)
+            scr.flags[k] = make_int2(q, sidx);
+          else  // the list is full: mark the pair for the host's next recompute round
+            P->scores[(int64_t)q * db.n + orig] = FLAG_SENTINEL;
         } else {
           P->scores[(int64_t)q * db.n + orig] = sb - go;
         }

@@ -18,6 +18,11 @@ constexpr int GROUP = 64;        // subjects per inter-task group (32 lanes x 2 
 constexpr int CHUNK = 8;         // residues per subject per interleaved chunk
 constexpr int CHUNK_BYTES = GROUP * CHUNK;  // 512 bytes: one chunk of a whole group
 constexpr int S16_LIMIT = 32767;
+// Score written for a saturated pair that found the flag list full; no
+// exact score is negative, so a later pass can find the pair by it.
+constexpr int32_t FLAG_SENTINEL = -1;
+// Default capacity of a plan's flag list (saturated pairs per search round).
+constexpr int64_t DEFAULT_FLAG_CAPACITY = 1 << 20;
 
 // ---- error reporting ----------------------------------------------------------
 sw_status sw_set_error(sw_status st, const char* fmt, ...);
@@ -120,6 +125,12 @@ size_t intra_smem_bytes(int rows);
 int intra_blocks_per_sm(int rows);
 cudaError_t launch_intra(const KernelConfig& kc, const DbView& db, const SearchParams* params,
                          SearchState* state, const Scratch& scr, cudaStream_t stream);
+
+// Flag-list overflow (intra_kernel.cu): appends every pair whose score in
+// P->scores is FLAG_SENTINEL to the flag list (up to its capacity, counting
+// all of them in state->n_flags), for a further round of the int32 kernel.
+cudaError_t launch_collect(int blocks, const DbView& db, const SearchParams* params,
+                           SearchState* state, const Scratch& scr, cudaStream_t stream);
 
 // Packed intra-task kernel over subject pairs, long subjects (pair_kernel.cu),
 // with 16 or 32 query rows per lane.

@@ -6,12 +6,15 @@ only schedules it.  A request is one query; its result is the exact score
 row against every subject.
 
 * The database stays resident on the device for the life of the server.
-* Admission: every request needs device memory for its scores row
-  (4 bytes x subjects) and its share of the plan's query/flag buffers; a
-  request is admitted while the bytes of all admitted, unfinished requests
-  stay within ``memory_budget`` (by default the bytes the slots hold, so
-  only an explicit, smaller budget holds requests back).  A request that could never fit is refused
-  at once (``AdmissionError``), never queued forever.
+* Admission: a request holds device memory while its batch runs: its scores
+  row (4 bytes x subjects), allocated when the batch is launched and freed
+  once the row is on the host, and its residues in the plan's query buffer.
+  A request is admitted while the bytes of all admitted, unfinished requests
+  stay within ``memory_budget``.  By default that is the smaller of what the
+  slots can hold with every batch full and 90% of the device memory free
+  when the server starts, so on a device that other work fills up, fewer
+  requests run at once.  A request that could never fit is refused at once
+  (``AdmissionError``), never queued forever.
 * Continuous batching: a scheduler thread takes the admitted requests that
   have arrived, up to ``max_batch`` queries and ``max_batch_residues``
   residues, and launches them as one batch on a free slot (its own plan and
@@ -63,20 +66,27 @@ class Request:
 
 
 class _Slot:
-    """One batch in flight: a plan, a CUDA stream and a device scores buffer.
+    """One batch in flight: a plan, a CUDA stream and the batch's scores.
 
     The scheduler talks to a slot only through ``launch``, ``poll``,
-    ``rows`` and ``close`` (and ``bind_thread`` once, on its own thread)."""
+    ``rows`` and ``close`` (and ``bind_thread`` once, on its own thread).
+    The scores buffer is allocated per batch, at its size, and released by
+    ``rows``, so the device memory a slot holds follows the admitted load."""
 
     def __init__(self, db, max_batch, max_residues, opts):
         import torch
         self.device = db.device
+        self.n = db.n
         self.plan = db.plan(max_batch, max_residues, **opts)
         self.stream = torch.cuda.Stream(device=db.device)
-        self.scores = torch.empty((max_batch, db.n), dtype=torch.int32,
-                                  device=f"cuda:{db.device}")
+        self.scores = None
         self.requests: list[Request] = []
         self.batch_id = -1
+
+    @staticmethod
+    def free_device_bytes(device) -> int:
+        import torch
+        return int(torch.cuda.mem_get_info(device)[0])
 
     @property
     def busy(self) -> bool:
@@ -88,16 +98,24 @@ class _Slot:
 
     def launch(self, queries, lengths, gap_open, gap_extend, matrix):
         """Queues the batch's search on the slot's stream."""
-        self.plan.search_async(queries, lengths, self.scores[:lengths.size], gap_open,
-                               gap_extend, matrix, stream=self.stream)
+        import torch
+        with torch.cuda.stream(self.stream):   # allocated for use on this stream
+            self.scores = torch.empty((lengths.size, self.n), dtype=torch.int32,
+                                      device=f"cuda:{self.device}")
+        self.plan.search_async(queries, lengths, self.scores, gap_open, gap_extend, matrix,
+                               stream=self.stream)
 
     def poll(self) -> bool:
         """True once the batch's scores are complete (raises if it failed)."""
         return self.plan.wait(0)
 
     def rows(self, n) -> np.ndarray:
-        """The finished batch's first n score rows, on the host."""
-        return self.scores[:n].cpu().numpy()
+        """The finished batch's first n score rows, on the host; the device
+        buffer is released."""
+        try:
+            return self.scores[:n].cpu().numpy()
+        finally:
+            self.scores = None
 
     def close(self):
         self.plan.close()
@@ -109,9 +127,11 @@ class Server:
     def __init__(self, db: swgb.Database, slots: int = 2, max_batch: int = 16,
                  max_batch_residues: int = 65536, memory_budget: int | None = None,
                  gap_open: int = 10, gap_extend: int = 2, matrix=None, slot_factory=None,
-                 **plan_opts):
+                 free_bytes=None, **plan_opts):
         """``slot_factory(db, max_batch, max_batch_residues, plan_opts)`` makes
-        one slot (default: a plan, a stream and a scores buffer on the GPU)."""
+        one slot (default: a plan and a stream on the GPU).  ``free_bytes()``
+        gives the device memory free at start (default: the CUDA driver's
+        figure with the default slots, no limit with a slot factory)."""
         self.db = db
         self.max_batch = int(max_batch)
         self.max_batch_residues = int(max_batch_residues)
@@ -119,13 +139,23 @@ class Server:
         make = slot_factory or _Slot
         self.slots = [make(db, self.max_batch, self.max_batch_residues, plan_opts)
                       for _ in range(int(slots))]
-        # default: what the slots hold, every slot's batch full (max_batch
-        # requests' score rows and flag shares, max_batch_residues residues)
-        self.memory_budget = int(memory_budget) if memory_budget else \
-            len(self.slots) * (self.max_batch * self.request_bytes(0) + self.max_batch_residues)
+        if free_bytes is None and slot_factory is None:
+            free_bytes = lambda: _Slot.free_device_bytes(db.device)  # noqa: E731
+        # default: what the slots hold with every batch full (max_batch score
+        # rows and max_batch_residues residues each), within 90% of the
+        # device memory free now that the slots' plans exist
+        full = len(self.slots) * (self.max_batch * self.request_bytes(0) + self.max_batch_residues)
+        self.free_at_start = int(free_bytes()) if free_bytes else None
+        if memory_budget:
+            self.memory_budget = int(memory_budget)
+        elif self.free_at_start is not None:
+            self.memory_budget = min(full, int(0.9 * self.free_at_start))
+        else:
+            self.memory_budget = full
         self._lock = threading.Condition()
         self._pending: collections.deque[Request] = collections.deque()
         self._in_use = 0
+        self.max_in_use = 0           # most bytes admitted at once
         self._next_id = 0
         self._batches = 0
         self.max_concurrent = 0       # most batches in flight at once
@@ -137,9 +167,11 @@ class Server:
 
     # ---- admission ------------------------------------------------------------
     def request_bytes(self, query_len: int) -> int:
-        """Device bytes a request holds while admitted: its scores row, its
-        residues in the query buffer and its saturation-list share."""
-        return 4 * self.db.n + int(query_len) + 8 * self.db.n
+        """Device bytes a request holds while admitted: its scores row and its
+        residues in the query buffer.  (The plan's border scratch and its
+        bounded saturation list are allocated once per slot, whatever the
+        load.)"""
+        return 4 * self.db.n + int(query_len)
 
     def submit(self, query, arrival: float | None = None) -> Future:
         q = np.ascontiguousarray(query, dtype=np.uint8)
@@ -180,6 +212,7 @@ class Server:
                 self.cancelled += 1
                 continue
             self._in_use += need
+            self.max_in_use = max(self.max_in_use, self._in_use)
             r.admitted = time.perf_counter()
             batch.append(r)
             residues += r.query.size
@@ -198,9 +231,23 @@ class Server:
         slot.launch(q, lens, self.gap_open, self.gap_extend, self.matrix)
         self.max_concurrent = max(self.max_concurrent, sum(s.busy for s in self.slots))
 
+    def _fail(self, slot, batch, e):
+        """A batch that failed fails its own requests only; its memory is released."""
+        with self._lock:
+            for r in batch:
+                self._in_use -= self.request_bytes(r.query.size)
+            slot.requests = []
+            self._lock.notify_all()
+        for r in batch:
+            r.future.set_exception(e)
+
     def _complete(self, slot: _Slot):
         batch = slot.requests
-        rows = slot.rows(len(batch))  # the slot's stream has finished
+        try:
+            rows = slot.rows(len(batch))  # the slot's stream has finished
+        except Exception as e:  # the copy to the host failed: like a failed search
+            self._fail(slot, batch, e)
+            return
         now = time.perf_counter()
         with self._lock:
             for i, r in enumerate(batch):
@@ -222,12 +269,7 @@ class Server:
                     try:
                         done = s.poll()
                     except Exception as e:  # a failed batch fails its requests only
-                        for r in s.requests:
-                            r.future.set_exception(e)
-                        with self._lock:
-                            for r in s.requests:
-                                self._in_use -= self.request_bytes(r.query.size)
-                            s.requests = []
+                        self._fail(s, s.requests, e)
                         progressed = True
                         continue
                     if done:
@@ -242,12 +284,7 @@ class Server:
                 try:
                     self._launch(free[0], batch)
                 except Exception as e:
-                    with self._lock:
-                        for r in batch:
-                            self._in_use -= self.request_bytes(r.query.size)
-                    free[0].requests = []
-                    for r in batch:
-                        r.future.set_exception(e)
+                    self._fail(free[0], batch, e)
                 progressed = True
             if not progressed:
                 with self._lock:
@@ -272,6 +309,7 @@ class Server:
                 "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
                 "mean_batch": len(self.completed) / max(self._batches, 1),
                 "max_concurrent_batches": self.max_concurrent, "cancelled": self.cancelled,
+                "memory_budget": self.memory_budget, "max_admitted_bytes": self.max_in_use,
                 "gcups": cells / wall_s / 1e9 if wall_s else None, "wall_s": wall_s}
 
 

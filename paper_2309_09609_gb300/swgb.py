@@ -39,7 +39,7 @@ class Options(ctypes.Structure):
                 ("use_graph", ctypes.c_int32), ("force_int32", ctypes.c_int32),
                 ("auto_cutoff", ctypes.c_int32), ("wide_min_len", ctypes.c_int32),
                 ("wide_min_subject", ctypes.c_int32), ("inter_columns", ctypes.c_int32),
-                ("overlap_kernels", ctypes.c_int32)]
+                ("overlap_kernels", ctypes.c_int32), ("flag_capacity", ctypes.c_int32)]
 
 
 class Alignment(ctypes.Structure):
@@ -51,7 +51,7 @@ class Alignment(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("cells", ctypes.c_int64), ("inter_items", ctypes.c_int64),
                 ("intra_items", ctypes.c_int64), ("recomputed_pairs", ctypes.c_int64),
-                ("timed_out", ctypes.c_int32), ("kernels_launched", ctypes.c_int32),
+                ("overflow_rounds", ctypes.c_int32), ("kernels_launched", ctypes.c_int32),
                 ("search_ms", ctypes.c_float), ("recompute_ms", ctypes.c_float),
                 ("pair_ms", ctypes.c_float), ("pad_", ctypes.c_int32),
                 ("inter_cells", ctypes.c_int64)]
@@ -419,15 +419,26 @@ def search_pairs_noalloc(queries, q_offsets, q_lengths, subjects, s_offsets, s_l
     for name, (x, dtype) in want.items():
         if not (hasattr(x, "data_ptr") and x.is_cuda and str(x.dtype) == "torch." + dtype):
             raise TypeError(f"{name} must be a {dtype} torch tensor on the GPU")
+    # the library launches on the current device: every tensor must live on
+    # one device, which is made current for the call
+    devices = {x.device.index for x, _ in want.values()}
+    if len(devices) != 1:
+        raise ValueError(f"all tensors must be on one GPU, got devices {sorted(devices)}")
     nq, ns = int(q_lengths.shape[0]), int(s_lengths.shape[0])
     if q_offsets.shape[0] != nq or s_offsets.shape[0] != ns:
         raise ValueError("one offset per sequence")
     scores = _scores_out(scores, nq, ns)
     m = None if matrix is None else _host(_matrix(matrix), "int8")   # host memory
-    _check(lib().sw_search_pairs_noalloc(
-        _ptr(queries), _ptr(q_offsets), _ptr(q_lengths), nq,
-        _ptr(subjects), _ptr(s_offsets), _ptr(s_lengths), ns,
-        gap_open, gap_extend, _ptr(m), _ptr(scores), _stream(stream)))
+    # an empty residue tensor may have no storage: pass NULL (allowed when
+    # every length on that side is 0; the library refuses to read it)
+    qp = _ptr(queries) if queries.numel() else None
+    sp = _ptr(subjects) if subjects.numel() else None
+    import torch
+    with torch.cuda.device(devices.pop()):
+        _check(lib().sw_search_pairs_noalloc(
+            qp, _ptr(q_offsets), _ptr(q_lengths), nq,
+            sp, _ptr(s_offsets), _ptr(s_lengths), ns,
+            gap_open, gap_extend, _ptr(m), _ptr(scores), _stream(stream)))
     return scores
 
 

@@ -78,6 +78,33 @@ def test_noalloc_wants_gpu_tensors_of_the_stated_types():
         swgb.search_pairs_noalloc(q.numpy(), off, ln, q, off, ln, sc)   # numpy
 
 
+class FakeCudaTensor:
+    """Stands in for a CUDA tensor on a given device (no GPU here): only the
+    attributes the binding's checks read."""
+
+    def __init__(self, dtype, n, index):
+        self.dtype, self.shape, self.is_cuda = dtype, (n,), True
+        self.device = type("Dev", (), {"index": index})()
+
+    def data_ptr(self):
+        return 0
+
+    def numel(self):
+        return self.shape[0]
+
+    def is_contiguous(self):
+        return True
+
+
+def test_noalloc_wants_every_tensor_on_one_device():
+    args = [FakeCudaTensor("torch.uint8", 4, 0), FakeCudaTensor("torch.int64", 1, 0),
+            FakeCudaTensor("torch.int32", 1, 0), FakeCudaTensor("torch.uint8", 4, 1),
+            FakeCudaTensor("torch.int64", 1, 0), FakeCudaTensor("torch.int32", 1, 0),
+            FakeCudaTensor("torch.int32", 1, 0)]
+    with pytest.raises(ValueError, match=r"one GPU, got devices \[0, 1\]"):
+        swgb.search_pairs_noalloc(*args)
+
+
 class FakeLib:
     """Stands in for libswgb.so: records every call, returns SW_OK.  Handles
     it creates stay NULL, so closing them is a no-op with any library."""

@@ -200,6 +200,39 @@ def test_saturation_with_large_matrix_entries():
     assert_exact(res, want)
 
 
+def test_flag_list_overflow_is_recomputed_in_rounds():
+    # Many saturated pairs against a flag list of 7 entries: the packed
+    # kernels mark the pairs that find it full, and rounds of the int32
+    # kernel after the search score them all exactly (through both the
+    # inter-task and the pair kernels: the cutoff sends subjects over 300
+    # residues to the latter).
+    rng = np.random.default_rng(17)
+    m = rand_matrix(rng, -20, 10)
+    np.fill_diagonal(m, 120)
+    base = seqset(rng, [420])
+    homologs = [synth.mutate(rng, base.res, 0.03) for _ in range(90)]
+    cut = [h[:int(k)] for h, k in zip(homologs, rng.integers(290, 421, 90))]
+    db = concat(synth.SeqSet(np.concatenate(cut), np.array([c.size for c in cut], np.int32)),
+                seqset(rng, rng.integers(5, 500, size=120)))
+    q = concat(base, seqset(rng, [60]), synth.SeqSet(base.res[:380], np.array([380], np.int32)))
+    want = oracle_all(q, db, 10, 2, m.astype(np.int32))
+    # flagged exactly when S + Go reaches 32767 - max(SM) (Go = 12)
+    n_sat = int((want + 12 >= 32767 - int(m.max())).sum())
+    assert n_sat > 100
+    d = swgb.Database.from_seqset(db)
+    for opts in (dict(flag_capacity=7, long_cutoff=300), dict(flag_capacity=7, use_graph=0)):
+        p = d.plan(len(q), q.total, **opts)
+        for _ in range(2):                                   # a plan reused after an overflow
+            got = p.search(q.res, q.lens, 10, 2, m)          # scores to host memory
+            st = p.stats()
+            assert st["recomputed_pairs"] == n_sat and st["overflow_rounds"] >= 10
+            assert_exact({"host": got}, want)
+        torch = pytest.importorskip("torch")
+        out = torch.full((len(q), len(db)), -5, dtype=torch.int32, device="cuda")
+        p.search(q.res, q.lens, 10, 2, m, out=out)          # scores to device memory
+        assert_exact({"device": out.cpu().numpy()}, want)
+
+
 @pytest.mark.parametrize("intra_rows", [8, 16])
 def test_recompute_spans_several_rounds_of_passes(intra_rows):
     # A flagged pair is recomputed by one block whose 16 warps take the query's

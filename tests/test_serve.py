@@ -3,7 +3,7 @@ admission, and identical results alone and in a mix."""
 import numpy as np
 import pytest
 
-from helpers import oracle_pairs, seqset
+from helpers import oracle_all, oracle_pairs, seqset
 from paper_2309_09609_gb300 import build as nvbuild
 from paper_2309_09609_gb300 import swgb, synth
 
@@ -64,3 +64,29 @@ def test_admission_refuses_what_can_never_fit(db):
             small.submit(np.zeros(10, np.uint8))           # budget below one scores row
     finally:
         small.close()
+
+
+def test_a_budget_below_the_offered_load_holds_requests_back(db):
+    """Twelve requests offered at once against a budget of two: at most two
+    are admitted at any time, the rest wait, and every score row equals the
+    oracle's on every subject."""
+    from paper_2309_09609_gb300 import serve
+    ss, d = db
+    rng = np.random.default_rng(4)
+    qs = seqset(rng, rng.integers(40, 151, 12))
+    srv = serve.Server(d, slots=2, max_batch=8, max_batch_residues=20000)
+    budget = 2 * srv.request_bytes(int(qs.lens.max()))
+    srv.close()
+    srv = serve.Server(d, slots=2, max_batch=8, max_batch_residues=20000, memory_budget=budget)
+    assert srv.free_at_start is not None and srv.free_at_start > budget
+    try:
+        with srv._lock:     # all twelve queued before the scheduler looks
+            futs = [srv.submit(qs.seq(i)) for i in range(len(qs))]
+        rows = np.stack([f.result(120) for f in futs])
+    finally:
+        srv.close()
+    assert srv.max_in_use <= budget
+    assert srv.report()["batches"] >= 6                 # never more than two per batch
+    assert max(sum(1 for r in srv.completed if r.batch == b)
+               for b in {r.batch for r in srv.completed}) <= 2
+    assert (rows == oracle_all(qs, ss)).all()

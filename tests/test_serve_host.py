@@ -31,8 +31,9 @@ class Gate:
 class FakeSlot:
     log = None          # the query lengths of every launched batch, in launch order
 
-    def __init__(self, gate, fail_launch=None, fail_poll=None):
+    def __init__(self, gate, fail_launch=None, fail_poll=None, fail_rows=None):
         self.gate, self.fail_launch, self.fail_poll = gate, fail_launch, fail_poll
+        self.fail_rows = fail_rows
         self.requests = []
         self.batch_id = -1
         self.rows_ = None
@@ -62,6 +63,8 @@ class FakeSlot:
         return True
 
     def rows(self, n):
+        if self.fail_rows is not None and self.fail_rows in self.lens:
+            raise RuntimeError("copy to the host failed")
         return self.rows_[:n]
 
     def close(self):
@@ -183,6 +186,45 @@ def test_a_failed_search_fails_only_its_own_batch():
     finally:
         srv.close()
     assert srv._in_use == 0
+
+
+def test_a_failed_copy_of_the_rows_fails_only_its_own_batch():
+    gate = Gate(True)
+    srv = server(gate, slots=1, max_batch=1, fail_rows=13)
+    try:
+        futs = [srv.submit(q) for q in queries([4, 13, 5])]
+        with pytest.raises(RuntimeError, match="copy to the host failed"):
+            futs[1].result(10)
+        assert (futs[0].result(10) == row_of(queries([4])[0])).all()
+        assert (futs[2].result(10) == row_of(queries([4, 13, 5])[2])).all()
+        # the scheduler thread is still alive and serving
+        assert srv.submit(queries([6])[0]).result(10).shape == (N_SUBJECTS,)
+    finally:
+        srv.close(timeout=10)
+    assert srv._in_use == 0 and not any(s.busy for s in srv.slots)
+
+
+def test_the_default_budget_stays_within_free_device_memory():
+    db = types.SimpleNamespace(n=N_SUBJECTS, device=0, residues=1)
+    FakeSlot.log = []
+    mk = lambda *a: FakeSlot(Gate(True))  # noqa: E731
+    roomy = serve.Server(db, slots=2, max_batch=3, max_batch_residues=30, slot_factory=mk,
+                         free_bytes=lambda: 10 ** 9)
+    tight = serve.Server(db, slots=2, max_batch=3, max_batch_residues=30, slot_factory=mk,
+                         free_bytes=lambda: 100)
+    try:
+        assert roomy.memory_budget == 2 * (3 * roomy.request_bytes(0) + 30)   # the slots full
+        assert tight.memory_budget == 90                                    # 90% of what is free
+        assert tight.free_at_start == 100
+        # two requests fit 90 bytes (4 x 7 + 10 each), a third waits for one to finish
+        per = tight.request_bytes(10)
+        assert 2 * per <= 90 < 3 * per
+        futs = [tight.submit(q) for q in queries([10] * 5)]
+        [f.result(10) for f in futs]
+        assert tight.max_in_use <= 90
+    finally:
+        roomy.close(timeout=10)
+        tight.close(timeout=10)
 
 
 def test_a_failed_launch_fails_only_its_own_batch():
