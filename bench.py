@@ -53,6 +53,9 @@ REF_CELLS = {"paper-search": 1.5e10, "batched-uneven": 1.5e10, "plain-small": 1.
 # (H'), viaddmax (E' next column), viaddmax (F' next row) and half a vimax3 (S);
 # H' - Go is an IMAD on the FMA pipe and is not counted
 PACKED_ALU_OPS_PER_CELL = 5.5 / 2
+# the same with two queries per word: the profile word is read ready-made,
+# so the prmt drops out (4.5 per word)
+TWO_QUERY_ALU_OPS_PER_CELL = 4.5 / 2
 
 
 def parse():
@@ -67,6 +70,9 @@ def parse():
     ap.add_argument("--cutoff", type=int, default=None, help="inter/intra length cutoff")
     ap.add_argument("--warps", type=int, default=None)
     ap.add_argument("--cols", type=int, default=None, help="inter-task wavefront columns (4/8)")
+    ap.add_argument("--two-query", type=int, default=None, choices=[0, 1, 2],
+                    help="two queries per word in the inter-task kernel: 0 never, 1 auto, 2 always")
+    ap.add_argument("--two-query-rows", type=int, default=None, choices=[16, 24, 32])
     ap.add_argument("--wide-min", type=int, default=None,
                     help="shortest query scored 32 rows per lane against long subjects")
     ap.add_argument("--wide-min-subject", type=int, default=None,
@@ -344,6 +350,8 @@ def profiled_traffic(args, kernel="inter_kernel"):
     default = (not args.subjects and not args.queries and args.rows in (None, 32)
                and args.warps in (None, 8) and args.cutoff in (None, 1500) and not args.tune
                and getattr(args, "cols", None) in (None, 8)
+               and getattr(args, "two_query", None) is None
+               and getattr(args, "two_query_rows", None) is None
                and getattr(args, "wide_min", None) is None
                and getattr(args, "wide_min_subject", None) is None)
     fname, srcs = TRAFFIC_RECORDS[key]
@@ -450,25 +458,30 @@ def roofline(t, peak, peak_source, rate_mhz, traffic):
     cell."""
     stats = t["stats"]
     per_kernel = {}
-    for name, kcells, kms_list in (
-            ("inter_kernel (packed inter-task)", stats["inter_cells"], t["kernel_ms"]),
-            ("pair_kernel (packed intra-task)", stats["cells"] - stats["inter_cells"], t["pair_ms"])):
+    two_q = stats.get("inter2_items", 0) > 0
+    inter_name = ("inter2q_kernel (packed inter-task, two queries per word)" if two_q
+                  else "inter_kernel (packed inter-task)")
+    for name, kcells, kms_list, ops in (
+            (inter_name, stats["inter_cells"], t["kernel_ms"],
+             TWO_QUERY_ALU_OPS_PER_CELL if two_q else PACKED_ALU_OPS_PER_CELL),
+            ("pair_kernel (packed intra-task)", stats["cells"] - stats["inter_cells"], t["pair_ms"],
+             PACKED_ALU_OPS_PER_CELL)):
         kms = statistics.mean(kms_list) if kms_list else float("nan")
-        ach = PACKED_ALU_OPS_PER_CELL * kcells / (kms / 1e3) / 1e12 if kcells else 0.0
+        ach = ops * kcells / (kms / 1e3) / 1e12 if kcells else 0.0
         per_kernel[name] = {"ms": round(kms, 3), "cells": int(kcells), "achieved": round(ach, 3),
-                            "frac": round(ach / peak, 4)}
+                            "frac": round(ach / peak, 4), "alu_ops_per_cell": ops}
     dominant = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
     dom = per_kernel[dominant]
-    inter = dominant.startswith("inter_kernel")
+    inter = dominant.startswith("inter")
     return {"bound": "alu", "achieved": dom["achieved"], "peak": round(peak, 3),
             "unit": "Tops/s", "frac": dom["frac"],
             "traffic": traffic("inter_kernel" if inter else "pair_kernel"),
             "kernel": dominant, "kernel_ms": dom["ms"], "kernel_cells": dom["cells"],
             "kernels": per_kernel,
-            "alu_ops_per_cell": PACKED_ALU_OPS_PER_CELL,
+            "alu_ops_per_cell": dom["alu_ops_per_cell"],
             "peak_source": peak_source,
             "intpeak_clock_mhz": round(rate_mhz, 1),
-            "peak_gcups": round(peak * 1e12 / PACKED_ALU_OPS_PER_CELL / 1e9, 1),
+            "peak_gcups": round(peak * 1e12 / dom["alu_ops_per_cell"] / 1e9, 1),
             "pair_kernel_ms": per_kernel["pair_kernel (packed intra-task)"]["ms"],
             "recompute_ms": round(statistics.mean(t["recompute_ms"]), 3)}
 
@@ -626,6 +639,10 @@ def run_native(args):
         opts["inter_columns"] = args.cols
     if args.no_graph:
         opts["use_graph"] = 0
+    if args.two_query is not None:
+        opts["two_query"] = args.two_query
+    if args.two_query_rows is not None:
+        opts["two_query_rows"] = args.two_query_rows
     if args.wide_min is not None:
         opts["wide_min_len"] = args.wide_min
     if args.wide_min_subject is not None:

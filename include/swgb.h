@@ -120,6 +120,12 @@ typedef struct {
                                 instead of after them, so its blocks take the SMs that their
                                 tails leave (lower latency for small searches); search_ms and
                                 pair_ms then overlap, both from the start; default 0 */
+  int32_t two_query;         /* inter-task scoring with two queries per 32-bit word against one
+                                subject per lane (no per-cell byte merge, 4.5 instead of 5.5
+                                ALU operations per word): 0 never, 1 when the plan's cost
+                                model expects it to be faster (default), 2 whenever a search
+                                has at least two queries */
+  int32_t two_query_rows;    /* query rows per strip of that kernel: 16, 24 or 32 (default) */
   int32_t flag_capacity;     /* entries of the plan's list of saturated pairs (8 bytes each);
                                 0: min(max_queries x subjects, 2^20).  More saturated pairs
                                 than this in one search are still scored exactly, in further
@@ -147,6 +153,8 @@ typedef struct {
                                 from their fork to their join (CUDA events) */
   int32_t pad_;
   int64_t inter_cells;       /* cells scored by the inter-task kernel */
+  int64_t inter2_items;      /* (stream pair, half group) items of the two-query inter-task
+                                kernel; 0 when the one-query kernel scored the short subjects */
 } sw_stats;
 
 /* Creates a search context for up to max_queries queries holding up to

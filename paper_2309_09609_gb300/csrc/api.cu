@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -113,6 +114,8 @@ extern "C" void sw_options_default(sw_options* opt) {
   opt->wide_min_subject = 4096;
   opt->inter_columns = 8;
   opt->overlap_kernels = 0;
+  opt->two_query = 1;
+  opt->two_query_rows = 32;
   opt->flag_capacity = 0;
 }
 
@@ -412,6 +415,7 @@ struct sw_plan {
   sw_db* db = nullptr;
   sw_options opt{};
   KernelConfig kc{};        // inter-task kernel
+  KernelConfig kc2{};       // inter-task kernel, two queries per word
   KernelConfig ikc{};       // int32 intra-task kernel
   int32_t max_queries = 0;
   int64_t max_residues = 0;
@@ -423,6 +427,10 @@ struct sw_plan {
   int64_t* qoff = nullptr;
   int32_t* qlen = nullptr;
   int32_t* qorder = nullptr;
+  int4* strips = nullptr;         // strip table of the two-query kernel
+  int2* spairs = nullptr;         // its stream pairs
+  int64_t strip_capacity = 0;
+  int32_t spair_capacity = 0;
   int32_t* scores_dev = nullptr;  // used when the caller's scores live on the host:
                                   // allocated by the first such search
   cudaStream_t stream = nullptr;  // the stream of the search in flight
@@ -436,6 +444,8 @@ struct sw_plan {
   int64_t* qoff_h = nullptr;
   int32_t* qlen_h = nullptr;
   int32_t* qorder_h = nullptr;
+  int4* strips_h = nullptr;
+  int2* spairs_h = nullptr;
   // graph
   cudaGraphExec_t graph = nullptr;
   cudaEvent_t done = nullptr;
@@ -470,6 +480,8 @@ static void plan_free(sw_plan* p) {
   cudaFree(p->qoff);
   cudaFree(p->qlen);
   cudaFree(p->qorder);
+  cudaFree(p->strips);
+  cudaFree(p->spairs);
   cudaFree(p->scores_dev);
   cudaFree(p->params);
   cudaFree(p->state);
@@ -483,6 +495,8 @@ static void plan_free(sw_plan* p) {
   cudaFreeHost(p->qoff_h);
   cudaFreeHost(p->qlen_h);
   cudaFreeHost(p->qorder_h);
+  cudaFreeHost(p->strips_h);
+  cudaFreeHost(p->spairs_h);
   cudaSetDevice(cur);
   delete p;
 }
@@ -510,6 +524,9 @@ extern "C" sw_status sw_plan_create(sw_db* db, int32_t max_queries, int64_t max_
   if (o.wide_min_len < 0 || o.wide_min_subject < 0)
     return sw_set_error(SW_EINVAL, "wide_min_len and wide_min_subject must be >= 0");
   if (o.flag_capacity < 0) return sw_set_error(SW_EINVAL, "flag_capacity < 0");
+  if (o.two_query < 0 || o.two_query > 2) return sw_set_error(SW_EINVAL, "two_query must be 0, 1 or 2");
+  if (o.two_query_rows != 16 && o.two_query_rows != 24 && o.two_query_rows != 32)
+    return sw_set_error(SW_EINVAL, "two_query_rows must be 16, 24 or 32");
   CUDA_TRY(cudaSetDevice(db->device));
 
   sw_plan* p = new sw_plan();
@@ -543,7 +560,22 @@ extern "C" sw_status sw_plan_create(sw_db* db, int32_t max_queries, int64_t max_
   p->kc.warps = o.warps_per_block;
   p->kc.blocks = dev_sms * bps;
   p->kc.smem = inter_smem_bytes(o.rows_per_thread, o.warps_per_block);
-  const int64_t W = (int64_t)p->kc.blocks * p->kc.warps;
+  // the two-query kernel: one block per SM, as many warps as its shared memory allows
+  const int warps2 = inter2q_warps(o.two_query_rows);
+  const int bps2 = inter2q_blocks_per_sm(o.two_query_rows, warps2);
+  if (bps2 < 1) {
+    plan_free(p);
+    return sw_set_error(SW_ECUDA, "two-query inter-task kernel cannot launch (rows %d)",
+                        o.two_query_rows);
+  }
+  p->kc2.variant = o.two_query_rows;
+  p->kc2.cols = 8;
+  p->kc2.warps = warps2;
+  p->kc2.blocks = dev_sms * bps2;
+  p->kc2.smem = inter2q_smem_bytes(o.two_query_rows, warps2);
+  // the two inter-task kernels run one after the other and share the border scratch
+  const int64_t W = std::max<int64_t>((int64_t)p->kc.blocks * p->kc.warps,
+                                      (int64_t)p->kc2.blocks * p->kc2.warps);
   // one block of INTRA_WARPS per SM: enough for the int32 items, and the
   // border scratch (one subject-length row per warp) stays bounded
   if (intra_blocks_per_sm(o.intra_rows) < 1) {
@@ -580,6 +612,12 @@ extern "C" sw_status sw_plan_create(sw_db* db, int32_t max_queries, int64_t max_
   if (e == cudaSuccess) e = dalloc(&p->qoff, max_queries);
   if (e == cudaSuccess) e = dalloc(&p->qlen, max_queries);
   if (e == cudaSuccess) e = dalloc(&p->qorder, 2 * (size_t)max_queries);  // qorder, then qpair
+  // strips: every query padded to 16-row strips (at least one), and as many
+  // empty halves at most; stream pairs: one per two queries at most
+  p->strip_capacity = 2 * (max_query_residues / 16 + 2 * (int64_t)max_queries) + 16;
+  p->spair_capacity = max_queries / 2 + 1;
+  if (e == cudaSuccess) e = dalloc(&p->strips, (size_t)p->strip_capacity);
+  if (e == cudaSuccess) e = dalloc(&p->spairs, (size_t)p->spair_capacity);
   if (e == cudaSuccess) e = dalloc(&p->params, 1);
   if (e == cudaSuccess) e = dalloc(&p->state, 1);
   if (e == cudaSuccess) e = dalloc(&p->scr.inter_border, (size_t)(W * std::max<int64_t>(p->scr.inter_stride_vec, 1)));
@@ -591,6 +629,8 @@ extern "C" sw_status sw_plan_create(sw_db* db, int32_t max_queries, int64_t max_
   if (e == cudaSuccess) e = cudaMallocHost((void**)&p->qoff_h, sizeof(int64_t) * max_queries);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&p->qlen_h, sizeof(int32_t) * max_queries);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&p->qorder_h, sizeof(int32_t) * 2 * max_queries);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&p->strips_h, sizeof(int4) * p->strip_capacity);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&p->spairs_h, sizeof(int2) * p->spair_capacity);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming);
   for (auto& ev : p->ev)
     if (e == cudaSuccess) e = cudaEventCreate(&ev);
@@ -644,6 +684,7 @@ static cudaError_t enqueue_kernels(sw_plan* p, cudaStream_t s, bool capturing) {
     // their tails
     if (e == cudaSuccess) e = cudaStreamWaitEvent(p->side2, p->fork, 0);
     if (e == cudaSuccess) e = launch_inter(p->kc, p->db->view, p->params, p->state, p->scr, p->side2);
+    if (e == cudaSuccess) e = launch_inter2q(p->kc2, p->db->view, p->params, p->state, p->scr, p->side2);
     if (e == cudaSuccess) e = record(p->ev[2], p->side2, capturing);
     if (e == cudaSuccess) e = cudaEventRecord(p->join2, p->side2);
   }
@@ -655,6 +696,7 @@ static cudaError_t enqueue_kernels(sw_plan* p, cudaStream_t s, bool capturing) {
     if (e == cudaSuccess) e = record(p->ev_join, s, capturing);
   } else {
     if (e == cudaSuccess) e = launch_inter(p->kc, p->db->view, p->params, p->state, p->scr, s);
+    if (e == cudaSuccess) e = launch_inter2q(p->kc2, p->db->view, p->params, p->state, p->scr, s);
     if (e == cudaSuccess) e = record(p->ev[2], s, capturing);
   }
   if (e == cudaSuccess) e = launch_intra(p->ikc, p->db->view, p->params, p->state, p->scr, s);
@@ -684,6 +726,81 @@ static cudaError_t run_kernels(sw_plan* p, cudaStream_t s) {
     }
   }
   return cudaGraphLaunch(p->graph, s);
+}
+
+// Two queries per word (inter2q_kernel.cu): deals the batch's queries to
+// 2K query streams, longest first, each to the stream with the fewest strips
+// so far (each query padded to whole strips of T rows, at least one), and
+// pairs streams 2k and 2k + 1.  Writes the strip table and the stream pairs
+// to the plan's pinned staging buffers.  Returns K, or 0 when the one-query
+// kernel should score the short subjects instead:
+//   * K is chosen for about 8 items per warp of the two-query kernel (items
+//     are stream pairs x group halves), at most nq / 2;
+//   * with option two_query = 1 the two-query layout must cost less than the
+//     one-query kernel's 32-row strips, counting a two-query word at 0.85 of
+//     a one-query word (4.5 + overhead against 5.5 + overhead ALU operations).
+static int32_t plan_streams(sw_plan* p, const HostBatch& hb, int32_t nq, int32_t groups,
+                            int64_t* n_strips) {
+  const int T = p->kc2.variant;
+  const double warps = (double)p->kc2.blocks * p->kc2.warps;
+  int32_t K = (int32_t)std::ceil(8.0 * warps / (2.0 * groups));
+  K = std::max(1, std::min(K, nq / 2));
+  std::vector<int64_t> strips_of((size_t)nq);
+  for (int32_t i = 0; i < nq; i++) strips_of[i] = std::max<int64_t>(1, (hb.len[i] + T - 1) / T);
+  // longest first (hb.order), each to the stream with the fewest strips
+  std::vector<std::vector<int32_t>> streams((size_t)2 * K);
+  std::vector<int64_t> load((size_t)2 * K, 0);
+  for (int32_t i = 0; i < nq; i++) {
+    const int32_t q = hb.order[i];
+    size_t best = 0;
+    for (size_t t = 1; t < load.size(); t++)
+      if (load[t] < load[best]) best = t;
+    streams[best].push_back(q);
+    load[best] += strips_of[q];
+  }
+  int64_t total = 0, cost2 = 0, cost1 = 0;
+  for (int32_t k = 0; k < K; k++) total += std::max(load[2 * k], load[2 * k + 1]);
+  if (total > p->strip_capacity) return 0;
+  cost2 = total * T;  // words per column and half-group: S_k strips x T rows
+  for (int32_t i = 0; i < nq; i++) cost1 += (hb.len[i] + 31) / 32 * 32;  // rows per column and group
+  // per column of a 64-subject group: one-query = cost1 words; two-query =
+  // 2 halves x cost2 words at 0.85 each
+  if (p->opt.two_query == 1 && 2.0 * 0.85 * (double)cost2 >= (double)cost1) return 0;
+  int64_t at = 0;
+  for (int32_t k = 0; k < K; k++) {
+    const int64_t S = std::max(load[2 * k], load[2 * k + 1]);
+    p->spairs_h[k] = make_int2((int32_t)at, (int32_t)S);
+    // each half walks its stream: query index, first row, end bit
+    int4* tab = p->strips_h + at;
+    for (int half = 0; half < 2; half++) {
+      const std::vector<int32_t>& st = streams[2 * k + half];
+      size_t qi = 0;
+      int64_t row = 0;
+      for (int64_t s = 0; s < S; s++) {
+        int32_t q = -1, first = 0;
+        if (qi < st.size()) {
+          q = st[qi];
+          first = (int32_t)row;
+          row += T;
+          if (row >= (int64_t)strips_of[q] * T) {  // this query's last strip
+            first |= (int32_t)0x80000000u;
+            ++qi;
+            row = 0;
+          }
+        }
+        if (half == 0) {
+          tab[s].x = q;
+          tab[s].y = first;
+        } else {
+          tab[s].z = q;
+          tab[s].w = first;
+        }
+      }
+    }
+    at += S;
+  }
+  *n_strips = at;
+  return K;
 }
 
 // Stages a batch into the plan and enqueues everything up to (not including)
@@ -754,6 +871,21 @@ static sw_status plan_enqueue(sw_plan* p, const HostBatch& hb, int32_t nq, int32
   P.nq_pair32 = n32;
   P.nq_pair16 = n16;
   P.n_inter_items = (int64_t)(v.groups - gf) * nq;
+  // two queries per word for the short subjects, when the plan's options and
+  // the cost model say so (the one-query kernel then has no items)
+  P.strips = p->strips;
+  P.spairs = p->spairs;
+  P.n_spairs = 0;
+  P.n_inter2_items = 0;
+  int64_t n_strips = 0;
+  if (packed && gf < v.groups && nq >= 2 && p->opt.two_query > 0) {
+    const int32_t K = plan_streams(p, hb, nq, v.groups - gf, &n_strips);
+    if (K > 0) {
+      P.n_spairs = K;
+      P.n_inter2_items = (int64_t)K * 2 * (v.groups - gf);
+      P.n_inter_items = 0;
+    }
+  }
   memcpy(p->qoff_h, hb.off.data(), sizeof(int64_t) * nq);
   memcpy(p->qlen_h, hb.len.data(), sizeof(int32_t) * nq);
   memcpy(p->qorder_h, hb.order.data(), sizeof(int32_t) * nq);
@@ -766,6 +898,10 @@ static sw_status plan_enqueue(sw_plan* p, const HostBatch& hb, int32_t nq, int32
     CUDA_TRY(cudaMemcpyAsync(p->qlen, p->qlen_h, sizeof(int32_t) * nq, cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(p->qorder, p->qorder_h, sizeof(int32_t) * 2 * nq, cudaMemcpyHostToDevice, s));
   }
+  if (P.n_spairs > 0) {
+    CUDA_TRY(cudaMemcpyAsync(p->strips, p->strips_h, sizeof(int4) * n_strips, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(p->spairs, p->spairs_h, sizeof(int2) * P.n_spairs, cudaMemcpyHostToDevice, s));
+  }
   CUDA_TRY(cudaMemcpyAsync(p->params, p->params_h, sizeof(SearchParams), cudaMemcpyHostToDevice, s));
   p->stream = s;
   CUDA_TRY(run_kernels(p, s));
@@ -774,9 +910,10 @@ static sw_status plan_enqueue(sw_plan* p, const HostBatch& hb, int32_t nq, int32
   int64_t qsum = hb.total;
   p->pending.cells = qsum * p->db->residues;
   p->pending.inter_items = P.n_inter_items;
+  p->pending.inter2_items = P.n_inter2_items;
   p->pending.intra_items = n_long * nq;  // (query, long subject) pairs, packed or int32
   p->pending.inter_cells = qsum * (p->db->residues - p->db->cres_h[n_long]);
-  p->pending.kernels_launched = 4;
+  p->pending.kernels_launched = 5;
   return SW_OK;
 }
 

@@ -61,9 +61,17 @@ struct SearchParams {
   const int32_t* qpair;   // [nq_pair32 + nq_pair16] query indices for the pair kernels:
                           // those of pair_kernel<32>, then those of pair_kernel<16>
   int32_t* scores;        // [nq x N] caller order
+  // two queries per word (inter2q_kernel.cu): the strip table, per strip
+  // (query of half 0, its first row | end bit 31, query of half 1, its first
+  // row | end bit 31), query -1 for an empty half; and per stream pair its
+  // first strip and strip count
+  const int4* strips;
+  const int2* spairs;
+  int64_t n_inter2_items; // stream pairs x 2 x inter groups (0: the one-query kernel runs)
   int64_t n_intra_items;  // n_long x nq  (int32 intra-task items, when the packed path is off)
   int64_t n_inter_items;  // inter groups x nq  (packed inter-task items)
   int32_t nq;
+  int32_t n_spairs;       // stream pairs of the two-query kernel
   int32_t pair_queries;   // nq when the packed path scores the long subjects, else 0
   int32_t n_wide_pairs;   // subject pairs [0, n_wide_pairs) may go to pair_kernel<32> ...
   int32_t nq_pair32;      // ... with these queries (qpair[0, nq_pair32)); the narrow
@@ -85,6 +93,7 @@ struct SearchState {
   unsigned long long pair_work;   // next work item (pair_kernel<16>)
   unsigned long long pair_work32; // next work item (pair_kernel<32>)
   unsigned long long intra_work;  // next int32 intra-task item (per warp)
+  unsigned long long work2;       // next work item (two-query inter-task kernel)
   unsigned int status;            // reserved: error bits raised on the device
   unsigned int pad;
 };
@@ -117,6 +126,14 @@ size_t inter_smem_bytes(int rows, int warps);
 int inter_blocks_per_sm(int rows, int cols, int warps);  // resident blocks per SM, 0 if none
 cudaError_t launch_inter(const KernelConfig& kc, const DbView& db, const SearchParams* params,
                          SearchState* state, const Scratch& scr, cudaStream_t stream);
+
+// Inter-task kernel with two queries per word (inter2q_kernel.cu), 16, 24 or
+// 32 rows per strip.
+size_t inter2q_smem_bytes(int rows, int warps);
+int inter2q_warps(int rows);  // warps per block (one block per SM)
+int inter2q_blocks_per_sm(int rows, int warps);  // resident blocks per SM, 0 if none
+cudaError_t launch_inter2q(const KernelConfig& kc, const DbView& db, const SearchParams* params,
+                           SearchState* state, const Scratch& scr, cudaStream_t stream);
 
 // Int32 intra-task kernel (intra_kernel.cu): int32 items one warp each, then
 // flagged pairs one block each.  Scratch: one border row per warp.

@@ -39,7 +39,8 @@ class Options(ctypes.Structure):
                 ("use_graph", ctypes.c_int32), ("force_int32", ctypes.c_int32),
                 ("auto_cutoff", ctypes.c_int32), ("wide_min_len", ctypes.c_int32),
                 ("wide_min_subject", ctypes.c_int32), ("inter_columns", ctypes.c_int32),
-                ("overlap_kernels", ctypes.c_int32), ("flag_capacity", ctypes.c_int32)]
+                ("overlap_kernels", ctypes.c_int32), ("two_query", ctypes.c_int32),
+                ("two_query_rows", ctypes.c_int32), ("flag_capacity", ctypes.c_int32)]
 
 
 class Alignment(ctypes.Structure):
@@ -54,7 +55,7 @@ class Stats(ctypes.Structure):
                 ("overflow_rounds", ctypes.c_int32), ("kernels_launched", ctypes.c_int32),
                 ("search_ms", ctypes.c_float), ("recompute_ms", ctypes.c_float),
                 ("pair_ms", ctypes.c_float), ("pad_", ctypes.c_int32),
-                ("inter_cells", ctypes.c_int64)]
+                ("inter_cells", ctypes.c_int64), ("inter2_items", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

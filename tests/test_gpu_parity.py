@@ -23,14 +23,25 @@ def built():
 
 
 def all_paths(q, db, go=10, ge=2, matrix=None, plain=True, **opts):
+    """Scores through every path: the one-shot search, a plan (twice: the
+    second replays its graph) with `opts`, the same plan forced to the
+    one-query and to the two-query inter-task kernel, and the plain
+    baseline.  Returns them with the stats of the `opts` plan."""
     d = swgb.Database.from_seqset(db)
     res = {"search": d.search(q.res, q.lens, go, ge, matrix)}
     p = d.plan(max(len(q), 1), max(q.total, 1), **opts)
     res["plan"] = p.search(q.res, q.lens, go, ge, matrix)
+    st = p.stats()
     res["plan_replay"] = p.search(q.res, q.lens, go, ge, matrix)
+    if "two_query" not in opts:
+        for tq in (0, 2):
+            pk = d.plan(max(len(q), 1), max(q.total, 1), two_query=tq, **opts)
+            res[f"plan_two_query_{tq}"] = pk.search(q.res, q.lens, go, ge, matrix)
+            if tq == 2 and len(q) >= 2 and st["inter_cells"] > 0 and not opts.get("force_int32"):
+                assert pk.stats()["inter2_items"] > 0 and pk.stats()["inter_items"] == 0
     if plain:
         res["plain"] = d.search_plain(q.res, q.lens, go, ge, matrix)
-    return res, p.stats()
+    return res, st
 
 
 def assert_exact(res, want):
@@ -58,6 +69,45 @@ def test_ragged_tiles(rows, cols, gaps):
     assert_exact(res, oracle_all(q, db, *gaps))
 
 
+@pytest.mark.parametrize("rows", [16, 24, 32])
+def test_two_query_streams_ragged(rows):
+    # Thirteen queries around the strip height (and of length 0 and 1) dealt
+    # to query streams: several stream pairs on a small database, queries
+    # changing inside a half, empty halves padding the shorter stream.
+    rng = np.random.default_rng(60 + rows)
+    q = seqset(rng, [0, 1, 5, rows - 1, rows, rows + 1, 2 * rows, 3 * rows - 1, 100, 333, 47,
+                     250, 8])
+    db = concat(seqset(rng, [0, 1, 7, 8, 9, 63, 64, 65]), seqset(rng, rng.integers(1, 700, 300)))
+    want = oracle_all(q, db)
+    d = swgb.Database.from_seqset(db)
+    res = {}
+    for sub in (q, q.subset([3, 9, 10])):   # many stream pairs; one pair of two streams
+        p = d.plan(len(sub), max(sub.total, 1), two_query=2, two_query_rows=rows)
+        got = p.search(sub.res, sub.lens)
+        st = p.stats()
+        assert st["inter2_items"] > 0 and st["inter_items"] == 0
+        res[len(sub)] = got
+    assert_exact({"13": res[13]}, want)
+    assert_exact({"3": res[3]}, want[[3, 9, 10]])
+
+
+@pytest.mark.parametrize("rows", [16, 24, 32])
+def test_two_query_saturation_in_one_half(rows):
+    # a saturating query beside ordinary ones: its half is flagged and
+    # recomputed, the other half of every word stays exact
+    rng = np.random.default_rng(70 + rows)
+    w = lambda k: "W" * k
+    q = concat(from_text(w(2990), w(2978) + "A" * 40, "HEAGAWGHEE"), seqset(rng, [30, 500, 2000]))
+    db = concat(from_text(w(2977), w(2978), w(3000) + "K" * 20), seqset(rng, rng.integers(1, 400, 200)))
+    want = oracle_all(q, db)
+    assert want.max() > 32767
+    d = swgb.Database.from_seqset(db)
+    p = d.plan(len(q), q.total, two_query=2, two_query_rows=rows, long_cutoff=4000)
+    got = p.search(q.res, q.lens)
+    assert p.stats()["recomputed_pairs"] >= 4 and p.stats()["inter2_items"] > 0
+    assert_exact({"2q": got}, want)
+
+
 def test_full_alphabet_and_asymmetric_matrix():
     rng = np.random.default_rng(3)
     m = rand_matrix(rng, -6, 9, symmetric=False)
@@ -75,7 +125,7 @@ def test_long_subjects_intra_task(intra_rows):
                 list(rng.integers(1, 61, size=130)))
     q = seqset(rng, [1, 31, 255, 256, 257, 300, 513, 700])
     res, st = all_paths(q, db, long_cutoff=64, intra_rows=intra_rows)
-    assert st["intra_items"] > 0 and st["inter_items"] > 0
+    assert st["intra_items"] > 0 and st["inter_items"] + st["inter2_items"] > 0
     # and every subject through the int32 intra-task kernel (several passes)
     d = swgb.Database.from_seqset(db)
     res["int32_intra"] = d.plan(len(q), q.total, force_int32=1, intra_rows=intra_rows).search(
@@ -131,7 +181,8 @@ def test_overlapped_kernels(wide_min_subject):
     want = oracle_all(q, db)
     res, st = all_paths(q, db, long_cutoff=550, plain=False, overlap_kernels=1,
                         wide_min_subject=wide_min_subject)
-    assert st["recomputed_pairs"] >= 1 and st["inter_items"] > 0 and st["intra_items"] > 0
+    assert st["recomputed_pairs"] >= 1 and st["intra_items"] > 0
+    assert st["inter_items"] + st["inter2_items"] > 0
     assert_exact(res, want)
 
 
@@ -220,7 +271,8 @@ def test_flag_list_overflow_is_recomputed_in_rounds():
     n_sat = int((want + 12 >= 32767 - int(m.max())).sum())
     assert n_sat > 100
     d = swgb.Database.from_seqset(db)
-    for opts in (dict(flag_capacity=7, long_cutoff=300), dict(flag_capacity=7, use_graph=0)):
+    for opts in (dict(flag_capacity=7, long_cutoff=300), dict(flag_capacity=7, use_graph=0),
+                 dict(flag_capacity=7, two_query=2), dict(flag_capacity=7, two_query=0)):
         p = d.plan(len(q), q.total, **opts)
         for _ in range(2):                                   # a plan reused after an overflow
             got = p.search(q.res, q.lens, 10, 2, m)          # scores to host memory
