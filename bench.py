@@ -310,13 +310,13 @@ CSRC = os.path.join(ROOT, "paper_2309_09609_gb300", "csrc")
 # while the kernel's own sources hash to the recorded value:
 # (kernel, workload) -> (record file, sources hashed in order)
 TRAFFIC_RECORDS = {
-    ("inter_kernel", "paper-search"): ("inter_kernel_paper-search_traffic.txt",
-                                       ("inter_kernel.cu", "device_common.cuh")),
+    ("inter2q_kernel", "paper-search"): ("inter2q_kernel_paper-search_traffic.txt",
+                                         ("inter2q_kernel.cu", "device_common.cuh")),
     ("pair_kernel", "long"): ("pair_kernel_long-sequences_traffic.txt",
                               ("pair_kernel.cu", "device_common.cuh")),
 }
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", TRAFFIC_RECORDS[("inter_kernel", "paper-search")][0])
-KERNEL_SOURCES = [os.path.join(CSRC, f) for f in TRAFFIC_RECORDS[("inter_kernel", "paper-search")][1]]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", TRAFFIC_RECORDS[("inter2q_kernel", "paper-search")][0])
+KERNEL_SOURCES = [os.path.join(CSRC, f) for f in TRAFFIC_RECORDS[("inter2q_kernel", "paper-search")][1]]
 
 
 def kernel_sources_sha256(sources=None):
@@ -340,7 +340,7 @@ def traffic_record(path=None):
     return rec
 
 
-def profiled_traffic(args, kernel="inter_kernel"):
+def profiled_traffic(args, kernel="inter2q_kernel"):
     """DRAM bytes per launch of the dominant kernel from its committed ncu
     record, if the record covers this workload at its default size and plan,
     and the kernel's sources are unchanged since the capture."""
@@ -475,7 +475,8 @@ def roofline(t, peak, peak_source, rate_mhz, traffic):
     inter = dominant.startswith("inter")
     return {"bound": "alu", "achieved": dom["achieved"], "peak": round(peak, 3),
             "unit": "Tops/s", "frac": dom["frac"],
-            "traffic": traffic("inter_kernel" if inter else "pair_kernel"),
+            "traffic": traffic(("inter2q_kernel" if two_q else "inter_kernel") if inter
+                               else "pair_kernel"),
             "kernel": dominant, "kernel_ms": dom["ms"], "kernel_cells": dom["cells"],
             "kernels": per_kernel,
             "alu_ops_per_cell": dom["alu_ops_per_cell"],

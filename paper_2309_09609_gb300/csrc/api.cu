@@ -734,8 +734,11 @@ static cudaError_t run_kernels(sw_plan* p, cudaStream_t s) {
 // pairs streams 2k and 2k + 1.  Writes the strip table and the stream pairs
 // to the plan's pinned staging buffers.  Returns K, or 0 when the one-query
 // kernel should score the short subjects instead:
-//   * K is chosen for about 8 items per warp of the two-query kernel (items
-//     are stream pairs x group halves), at most nq / 2;
+//   * K is the smallest count giving at least 4 items per warp of the
+//     two-query kernel (items are stream pairs x group halves), at most
+//     nq / 2: fewer, longer streams pad less (a stream pair is as long as
+//     its longer stream), and items run longest group first, so the last
+//     ones are short;
 //   * with option two_query = 1 the two-query layout must cost less than the
 //     one-query kernel's 32-row strips, counting a two-query word at 0.85 of
 //     a one-query word (4.5 + overhead against 5.5 + overhead ALU operations).
@@ -743,7 +746,7 @@ static int32_t plan_streams(sw_plan* p, const HostBatch& hb, int32_t nq, int32_t
                             int64_t* n_strips) {
   const int T = p->kc2.variant;
   const double warps = (double)p->kc2.blocks * p->kc2.warps;
-  int32_t K = (int32_t)std::ceil(8.0 * warps / (2.0 * groups));
+  int32_t K = (int32_t)std::ceil(4.0 * warps / (2.0 * groups));
   K = std::max(1, std::min(K, nq / 2));
   std::vector<int64_t> strips_of((size_t)nq);
   for (int32_t i = 0; i < nq; i++) strips_of[i] = std::max<int64_t>(1, (hb.len[i] + T - 1) / T);

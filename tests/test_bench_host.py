@@ -11,7 +11,8 @@ import bench  # noqa: E402
 
 def _args(**kw):
     base = dict(workload="paper-search", subjects=None, queries=None, rows=None, warps=None,
-                cutoff=None, tune=False, wide_min=None, wide_min_subject=None)
+                cutoff=None, tune=False, wide_min=None, wide_min_subject=None, two_query=None,
+                two_query_rows=None)
     base.update(kw)
     return argparse.Namespace(**base)
 
@@ -29,6 +30,12 @@ def test_traffic_record_applies_only_to_the_profiled_kernel_and_workload():
     assert bench.profiled_traffic(_args(cutoff=3000)) is None
     assert bench.profiled_traffic(_args(workload="long")) is None        # not the inter kernel's
     assert bench.profiled_traffic(_args(workload="batched-uneven"), "pair_kernel") is None
+    assert bench.profiled_traffic(_args(), "inter_kernel") is None      # no record of that kernel
+    assert bench.profiled_traffic(_args(two_query=0)) is None
+    long = bench.profiled_traffic(_args(workload="long"), "pair_kernel")
+    rec = bench.traffic_record(os.path.join(ROOT, "profiles",
+                                            bench.TRAFFIC_RECORDS[("pair_kernel", "long")][0]))
+    assert long is None or long == int(rec["dram_bytes_per_launch"])
 
 
 def test_workload_query_subset():
