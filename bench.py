@@ -101,6 +101,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-align", action="store_true", help="skip the traceback leg")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-shard", action="store_true",
+                    help="under several ranks, skip the one-search-over-all-ranks leg")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the batched-uneven and long-sequence records of the default run")
     ap.add_argument("--config-steps", type=int, default=2,
@@ -613,6 +615,36 @@ def run_config(name, args, device, local, stream, peak, peak_src, rate_mhz):
     return rec
 
 
+def run_sharded(args, rank, world, local, device, dist, one_gpu_scores):
+    """The one-GPU workload (seed, not seed + rank) as ONE search over all
+    ranks: each rank scores its cell-weighted partition of the database, and
+    the int32 columns are all-gathered in caller order.  Timed between
+    barriers, all-gather included, max over ranks.  Rank 0 checks the
+    gathered matrix against its own one-GPU search of the same workload."""
+    import torch
+    from paper_2309_09609_gb300 import shard
+    w = make_workload(args.workload, args.seed, args.subjects, args.queries, args.query_offset)
+    sd = shard.ShardedDatabase(w.db, dist, device=local)
+    sd.search(w.queries.res, w.queries.lens, w.gap_open, w.gap_extend)      # warm-up
+    dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        got = sd.search(w.queries.res, w.queries.lens, w.gap_open, w.gap_extend)
+    torch.cuda.synchronize()
+    dist.barrier()
+    ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / args.steps, dist, device)
+    rec = {"value": round(w.cells / (ms / 1e3) / 1e9, 2), "unit": "GCUPS",
+           "ms_per_step": round(ms, 3), "scaling": "strong", "steps": args.steps,
+           "subjects_per_rank": sd.sizes.tolist(),
+           "residues_per_rank": [int(w.db.lens[sd.bounds[r]:sd.bounds[r + 1]].sum())
+                                 for r in range(world)],
+           "note": "host clock around search + all-gather of the int32 columns (host buffers)"}
+    if one_gpu_scores is not None:
+        rec["equals_one_gpu"] = bool((one_gpu_scores.cpu().numpy() == got).all())
+    return rec
+
+
 def run_native(args):
     import torch
     rank, world, local, dist = dist_setup(args)
@@ -713,6 +745,12 @@ def run_native(args):
     result["e2e"] = {"value": round(all_cells / e2e_s / 1e9, 2), "unit": "GCUPS",
                      "h2d_bytes_per_step": int(q.total + 4 * nq),
                      "d2h_bytes_per_step": int(4 * nq * N), "ms_per_step": round(1e3 * e2e_s, 3)}
+
+    # one search split over the ranks (database sharded by cells, columns
+    # all-gathered): strong scaling of the rank-0 workload
+    if world > 1 and not args.no_shard:
+        result["sharded"] = run_sharded(args, rank, world, local, device, dist,
+                                        out if rank == 0 else None)
 
     # traceback of each query's best hit (sw_align), checked against the oracle
     if rank == 0 and world == 1 and args.workload in ("paper-search", "plain-small") and not args.no_align:
