@@ -740,8 +740,10 @@ static cudaError_t run_kernels(sw_plan* p, cudaStream_t s) {
 //     its longer stream), and items run longest group first, so the last
 //     ones are short;
 //   * with option two_query = 1 the two-query layout must cost less than the
-//     one-query kernel's 32-row strips, counting a two-query word at 0.85 of
-//     a one-query word (4.5 + overhead against 5.5 + overhead ALU operations).
+//     one-query kernel's 32-row strips, counting a two-query word at 0.9 of a
+//     one-query word: measured 0.88 on the paper-shaped search (20 queries)
+//     and 0.93 on a search of two queries (375 and 455 residues), where the
+//     one-query kernel is then the faster.
 static int32_t plan_streams(sw_plan* p, const HostBatch& hb, int32_t nq, int32_t groups,
                             int64_t* n_strips) {
   const int T = p->kc2.variant;
@@ -768,7 +770,7 @@ static int32_t plan_streams(sw_plan* p, const HostBatch& hb, int32_t nq, int32_t
   for (int32_t i = 0; i < nq; i++) cost1 += (hb.len[i] + 31) / 32 * 32;  // rows per column and group
   // per column of a 64-subject group: one-query = cost1 words; two-query =
   // 2 halves x cost2 words at 0.85 each
-  if (p->opt.two_query == 1 && 2.0 * 0.85 * (double)cost2 >= (double)cost1) return 0;
+  if (p->opt.two_query == 1 && 2.0 * 0.9 * (double)cost2 >= (double)cost1) return 0;
   int64_t at = 0;
   for (int32_t k = 0; k < K; k++) {
     const int64_t S = std::max(load[2 * k], load[2 * k + 1]);
