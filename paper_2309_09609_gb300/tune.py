@@ -1,18 +1,35 @@
 """Autotuner for the search plan's tile shape.
 
-Candidates: query rows per thread of the packed kernel (16, 32), columns per
-wavefront with 32 rows (4, 8), warps per block (4, 8), the inter/intra length
-cutoff, and rows per lane of the int32 intra-task kernel (8, 16).  None of
-them changes a score; they change speed only.  Each candidate runs a plan
-over a length-stratified sample of the batch's queries against the whole
-resident database and is timed by the plan's own CUDA events around all of
-its kernels (pair, inter-task and recompute).  The best is cached in a JSON
-file keyed by GPU, SM count, database signature, the sample's query length
-profile and the gap penalties.
+The options (all of which change speed only, never a score):
+
+* two queries per word in the inter-task kernel (``two_query``: by the
+  plan's cost model, or never) and that kernel's strip height (32, 24, 16
+  rows);
+* the one-query inter-task kernel's rows per thread (32, 16), columns per
+  wavefront with 32 rows (8, 4) and warps per block (8, 4);
+* the inter/intra length cutoff (1500, 3000, 7000, none) and the rows per
+  lane of the int32 intra-task kernel (8, 16).
+
+The search is a coordinate descent from the defaults: for each option in
+turn every alternative value is timed with the others at their best so far,
+and the best is kept; a second pass repeats this, and stops early once a
+pass changes nothing.  No option set is timed twice.  On the batched-uneven
+workload that is 15-20 searches of the sample instead of the 90 of the full
+product.  Each candidate runs a plan over a length-stratified sample of the
+batch's queries against the whole resident database and is timed by the
+plan's own CUDA events around all of its kernels (pair, inter-task and
+recompute).  The best is cached in a JSON file keyed by GPU, SM count,
+database signature, the sample's query length profile and the gap penalties.
+
+One shape serves the whole batch: the search is one persistent launch per
+kernel over every (query, subject-group) item, so its kernels run one
+configuration.  What does differ per length bucket is decided per item by
+the plan itself: which subjects go to the pair kernels (the cutoff), which
+pair-kernel width a query takes, and how queries are dealt to query
+streams.
 """
 from __future__ import annotations
 
-import itertools
 import json
 import os
 import threading
@@ -22,12 +39,75 @@ import numpy as np
 from . import swgb
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "swgb", "tune.json")
-ROWS = (16, 32)
-WARPS = (4, 8)
-CUTOFFS = (1500, 3000, 7000, 1 << 30)
-INTRA_ROWS = (8, 16)
-COLS = (4, 8)
+NO_CUTOFF = 1 << 30
 _lock = threading.Lock()
+
+
+def space(db, n_queries: int) -> dict:
+    """The values of each option, defaults first.  Cutoffs at or above the
+    longest subject collapse into "none"; the int32 row count matters only
+    when some cutoff sends subjects to the pair kernels (for their saturated
+    pairs); the two-query options only with two or more queries."""
+    maxlen = db.max_length
+    cuts = []
+    for c in (1500, 3000, 7000, NO_CUTOFF):
+        c = c if c < maxlen else NO_CUTOFF
+        if c not in cuts:
+            cuts.append(c)
+    sp = {}
+    if n_queries >= 2:
+        sp["two_query"] = [1, 0]
+        sp["two_query_rows"] = [32, 24, 16]
+    sp["rows_per_thread"] = [32, 16]
+    sp["inter_columns"] = [8, 4]
+    sp["warps_per_block"] = [8, 4]
+    sp["long_cutoff"] = cuts
+    if cuts[0] < maxlen:
+        sp["intra_rows"] = [8, 16]
+    return sp
+
+
+def valid(opt: dict) -> bool:
+    """Eight columns per wavefront need 32 rows per thread."""
+    return not (opt.get("rows_per_thread") == 16 and opt.get("inter_columns") == 8)
+
+
+def descend(sp: dict, measure, passes: int = 2):
+    """Coordinate descent over the option space `sp` (option -> values,
+    default first): returns (best options, [(options, cost), ...] in the
+    order timed).  `measure(options)` gives a cost, or None when the option
+    set cannot run; invalid sets are skipped and none is measured twice."""
+    seen = {}
+    order = []
+
+    def cost(opt):
+        key = tuple(sorted(opt.items()))
+        if key not in seen:
+            c = measure(dict(opt)) if valid(opt) else None
+            seen[key] = c
+            if c is not None:
+                order.append((dict(opt), c))
+        return seen[key]
+
+    best = {k: v[0] for k, v in sp.items()}
+    if not valid(best):
+        best["inter_columns"] = 4
+    best_cost = cost(best)
+    if best_cost is None:
+        raise RuntimeError("the default tile shape cannot run")
+    for _ in range(passes):
+        changed = False
+        for name, values in sp.items():
+            for v in values:
+                if v == best[name]:
+                    continue
+                trial = dict(best, **{name: v})
+                c = cost(trial)
+                if c is not None and c < best_cost:
+                    best, best_cost, changed = trial, c, True
+        if not changed:
+            break
+    return best, order
 
 
 def sample_queries(queries, k: int = 8):
@@ -38,22 +118,6 @@ def sample_queries(queries, k: int = 8):
     order = np.argsort(queries.lens, kind="stable")
     idx = order[np.unique(np.linspace(0, n - 1, k).round().astype(int))]
     return queries.subset(idx), idx
-
-
-def candidates(db: swgb.Database, rows=ROWS, warps=WARPS, cutoffs=CUTOFFS, intra_rows=INTRA_ROWS,
-               cols=COLS):
-    """Distinct option sets: cutoffs at or above the longest subject are one,
-    and 16 rows per thread have one column count (4)."""
-    maxlen = db.max_length
-    cuts = sorted({c if c < maxlen else 1 << 30 for c in cutoffs})
-    out = []
-    for r, w, c in itertools.product(rows, warps, cuts):
-        irs = intra_rows if c < maxlen else intra_rows[:1]
-        for ir in irs:
-            for k in (cols if r == 32 else (4,)):
-                out.append(dict(rows_per_thread=r, warps_per_block=w, long_cutoff=c, intra_rows=ir,
-                                inter_columns=k))
-    return out
 
 
 def _key(db, sample, gap_open, gap_extend) -> str:
@@ -74,7 +138,8 @@ def _load(path):
 
 
 def tune(db: swgb.Database, queries, gap_open: int = 10, gap_extend: int = 2,
-         cands=None, repeats: int = 2, cache: str | None = DEFAULT_CACHE, sample_size: int = 8):
+         repeats: int = 2, cache: str | None = DEFAULT_CACHE, sample_size: int = 8,
+         passes: int = 2):
     """Returns {"options": best option dict, "timings": [(options, ms), ...],
     "key": cache key, "cached": bool}."""
     import torch
@@ -86,16 +151,15 @@ def tune(db: swgb.Database, queries, gap_open: int = 10, gap_extend: int = 2,
         if hit:
             return {"options": hit["options"], "timings": hit.get("timings", []), "key": key,
                     "cached": True}
-    cands = cands or candidates(db)
     q = torch.from_numpy(sample.res).cuda(db.device)
     ql = torch.from_numpy(sample.lens).cuda(db.device)
     out = torch.empty((len(sample), db.n), dtype=torch.int32, device=f"cuda:{db.device}")
-    timings = []
-    for opt in cands:
+
+    def measure(opt):
         try:
             plan = db.plan(len(sample), max(sample.total, 1), **opt)
         except swgb.SwError:
-            continue  # e.g. a shape that cannot launch on this device
+            return None  # e.g. a shape that cannot launch on this device
         plan.search(q, ql, gap_open, gap_extend, out=out)  # warm-up (graph capture)
         best = float("inf")
         for _ in range(repeats):
@@ -104,10 +168,9 @@ def tune(db: swgb.Database, queries, gap_open: int = 10, gap_extend: int = 2,
             # the whole search: the cutoff moves work between the kernels
             best = min(best, st["pair_ms"] + st["search_ms"] + st["recompute_ms"])
         plan.close()
-        timings.append((opt, best))
-    if not timings:
-        raise RuntimeError("no candidate tile shape could run")
-    best_opt = min(timings, key=lambda t: t[1])[0]
+        return best
+
+    best_opt, timings = descend(space(db, len(sample)), measure, passes)
     if cache:
         with _lock:
             os.makedirs(os.path.dirname(cache), exist_ok=True)
