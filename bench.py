@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--two-query", type=int, default=None, choices=[0, 1, 2],
                     help="two queries per word in the inter-task kernel: 0 never, 1 auto, 2 always")
     ap.add_argument("--two-query-rows", type=int, default=None, choices=[16, 24, 32])
+    ap.add_argument("--two-query-pairs", type=int, default=None,
+                    help="stream pairs of the two-query kernel (default: the plan's choice)")
     ap.add_argument("--wide-min", type=int, default=None,
                     help="shortest query scored 32 rows per lane against long subjects")
     ap.add_argument("--wide-min-subject", type=int, default=None,
@@ -354,6 +356,7 @@ def profiled_traffic(args, kernel="inter2q_kernel"):
                and getattr(args, "cols", None) in (None, 8)
                and getattr(args, "two_query", None) is None
                and getattr(args, "two_query_rows", None) is None
+               and getattr(args, "two_query_pairs", None) is None
                and getattr(args, "wide_min", None) is None
                and getattr(args, "wide_min_subject", None) is None)
     fname, srcs = TRAFFIC_RECORDS[key]
@@ -676,6 +679,8 @@ def run_native(args):
         opts["two_query"] = args.two_query
     if args.two_query_rows is not None:
         opts["two_query_rows"] = args.two_query_rows
+    if args.two_query_pairs is not None:
+        opts["two_query_pairs"] = args.two_query_pairs
     if args.wide_min is not None:
         opts["wide_min_len"] = args.wide_min
     if args.wide_min_subject is not None:

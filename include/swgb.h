@@ -126,6 +126,8 @@ typedef struct {
                                 model expects it to be faster (default), 2 whenever a search
                                 has at least two queries */
   int32_t two_query_rows;    /* query rows per strip of that kernel: 16, 24 or 32 (default) */
+  int32_t two_query_pairs;   /* stream pairs of that kernel (0: the plan's choice, see
+                                sw_plan_search; otherwise at most n_queries / 2) */
   int32_t flag_capacity;     /* entries of the plan's list of saturated pairs (8 bytes each);
                                 0: min(max_queries x subjects, 2^20).  More saturated pairs
                                 than this in one search are still scored exactly, in further

@@ -116,6 +116,7 @@ extern "C" void sw_options_default(sw_options* opt) {
   opt->overlap_kernels = 0;
   opt->two_query = 1;
   opt->two_query_rows = 32;
+  opt->two_query_pairs = 0;
   opt->flag_capacity = 0;
 }
 
@@ -527,6 +528,7 @@ extern "C" sw_status sw_plan_create(sw_db* db, int32_t max_queries, int64_t max_
   if (o.two_query < 0 || o.two_query > 2) return sw_set_error(SW_EINVAL, "two_query must be 0, 1 or 2");
   if (o.two_query_rows != 16 && o.two_query_rows != 24 && o.two_query_rows != 32)
     return sw_set_error(SW_EINVAL, "two_query_rows must be 16, 24 or 32");
+  if (o.two_query_pairs < 0) return sw_set_error(SW_EINVAL, "two_query_pairs < 0");
   CUDA_TRY(cudaSetDevice(db->device));
 
   sw_plan* p = new sw_plan();
@@ -734,37 +736,58 @@ static cudaError_t run_kernels(sw_plan* p, cudaStream_t s) {
 // pairs streams 2k and 2k + 1.  Writes the strip table and the stream pairs
 // to the plan's pinned staging buffers.  Returns K, or 0 when the one-query
 // kernel should score the short subjects instead:
-//   * K is the smallest count giving at least 4 items per warp of the
-//     two-query kernel (items are stream pairs x group halves), at most
-//     nq / 2: fewer, longer streams pad less (a stream pair is as long as
-//     its longer stream), and items run longest group first, so the last
-//     ones are short;
+//   * K (unless the option fixes it) is the smallest power of two, at most
+//     nq / 2, for which the largest item -- the longest group against the
+//     longest stream pair -- is at most 0.35 of one warp's share of the
+//     search: fewer, longer streams pad less (a stream pair is as long as
+//     its longer stream), but an item longer than a warp's share finishes
+//     late; items run longest group first, so the last ones are short;
 //   * with option two_query = 1 the two-query layout must cost less than the
 //     one-query kernel's 32-row strips, counting a two-query word at 0.9 of a
 //     one-query word: measured 0.88 on the paper-shaped search (20 queries)
 //     and 0.93 on a search of two queries (375 and 455 residues), where the
 //     one-query kernel is then the faster.
-static int32_t plan_streams(sw_plan* p, const HostBatch& hb, int32_t nq, int32_t groups,
+static int32_t plan_streams(sw_plan* p, const HostBatch& hb, int32_t nq, int32_t g_first,
                             int64_t* n_strips) {
   const int T = p->kc2.variant;
   const double warps = (double)p->kc2.blocks * p->kc2.warps;
-  int32_t K = (int32_t)std::ceil(4.0 * warps / (2.0 * groups));
-  K = std::max(1, std::min(K, nq / 2));
+  const DbView& v = p->db->view;
+  double glen_sum = 0;
+  for (int32_t g = g_first; g < v.groups; g++) glen_sum += p->db->glen_h[g];
+  const double glen_max = g_first < v.groups ? p->db->glen_h[g_first] : 0.0;
   std::vector<int64_t> strips_of((size_t)nq);
   for (int32_t i = 0; i < nq; i++) strips_of[i] = std::max<int64_t>(1, (hb.len[i] + T - 1) / T);
   // longest first (hb.order), each to the stream with the fewest strips
-  std::vector<std::vector<int32_t>> streams((size_t)2 * K);
-  std::vector<int64_t> load((size_t)2 * K, 0);
-  for (int32_t i = 0; i < nq; i++) {
-    const int32_t q = hb.order[i];
-    size_t best = 0;
-    for (size_t t = 1; t < load.size(); t++)
-      if (load[t] < load[best]) best = t;
-    streams[best].push_back(q);
-    load[best] += strips_of[q];
+  std::vector<std::vector<int32_t>> streams;
+  std::vector<int64_t> load;
+  auto deal = [&](int32_t K) {
+    streams.assign((size_t)2 * K, {});
+    load.assign((size_t)2 * K, 0);
+    for (int32_t i = 0; i < nq; i++) {
+      const int32_t q = hb.order[i];
+      size_t best = 0;
+      for (size_t t = 1; t < load.size(); t++)
+        if (load[t] < load[best]) best = t;
+      streams[best].push_back(q);
+      load[best] += strips_of[q];
+    }
+  };
+  auto pair_strips = [&](int32_t k) { return std::max(load[2 * k], load[2 * k + 1]); };
+  int32_t K = p->opt.two_query_pairs > 0 ? std::min(p->opt.two_query_pairs, nq / 2) : 1;
+  deal(K);
+  while (p->opt.two_query_pairs == 0 && 2 * K <= nq / 2) {
+    int64_t smax = 0, ssum = 0;
+    for (int32_t k = 0; k < K; k++) {
+      smax = std::max(smax, pair_strips(k));
+      ssum += pair_strips(k);
+    }
+    // largest item vs a warp's share, both in (columns x strips) units
+    if (glen_max * (double)smax <= 0.35 * glen_sum * (double)ssum / warps) break;
+    K *= 2;
+    deal(K);
   }
   int64_t total = 0, cost2 = 0, cost1 = 0;
-  for (int32_t k = 0; k < K; k++) total += std::max(load[2 * k], load[2 * k + 1]);
+  for (int32_t k = 0; k < K; k++) total += pair_strips(k);
   if (total > p->strip_capacity) return 0;
   cost2 = total * T;  // words per column and half-group: S_k strips x T rows
   for (int32_t i = 0; i < nq; i++) cost1 += (hb.len[i] + 31) / 32 * 32;  // rows per column and group
@@ -884,7 +907,7 @@ static sw_status plan_enqueue(sw_plan* p, const HostBatch& hb, int32_t nq, int32
   P.n_inter2_items = 0;
   int64_t n_strips = 0;
   if (packed && gf < v.groups && nq >= 2 && p->opt.two_query > 0) {
-    const int32_t K = plan_streams(p, hb, nq, v.groups - gf, &n_strips);
+    const int32_t K = plan_streams(p, hb, nq, gf, &n_strips);
     if (K > 0) {
       P.n_spairs = K;
       P.n_inter2_items = (int64_t)K * 2 * (v.groups - gf);

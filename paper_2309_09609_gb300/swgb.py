@@ -40,7 +40,8 @@ class Options(ctypes.Structure):
                 ("auto_cutoff", ctypes.c_int32), ("wide_min_len", ctypes.c_int32),
                 ("wide_min_subject", ctypes.c_int32), ("inter_columns", ctypes.c_int32),
                 ("overlap_kernels", ctypes.c_int32), ("two_query", ctypes.c_int32),
-                ("two_query_rows", ctypes.c_int32), ("flag_capacity", ctypes.c_int32)]
+                ("two_query_rows", ctypes.c_int32), ("two_query_pairs", ctypes.c_int32),
+                ("flag_capacity", ctypes.c_int32)]
 
 
 class Alignment(ctypes.Structure):
