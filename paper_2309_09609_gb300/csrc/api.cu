@@ -447,8 +447,9 @@ struct sw_plan {
   int32_t* qorder_h = nullptr;
   int4* strips_h = nullptr;
   int2* spairs_h = nullptr;
-  // graph
-  cudaGraphExec_t graph = nullptr;
+  // graphs, one per gap class (the packed kernels are compiled per class)
+  cudaGraphExec_t graphs[GAP_CLASSES] = {};
+  int gclass = 0;  // gap class of the search being staged
   cudaEvent_t done = nullptr;
   // before the pair kernel, before and after the inter-task kernel, after recompute
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -467,7 +468,8 @@ static void plan_free(sw_plan* p) {
   int cur = 0;
   cudaGetDevice(&cur);
   if (p->db) cudaSetDevice(p->db->device);
-  if (p->graph) cudaGraphExecDestroy(p->graph);
+  for (auto& g : p->graphs)
+    if (g) cudaGraphExecDestroy(g);
   if (p->done) cudaEventDestroy(p->done);
   for (auto& e : p->ev)
     if (e) cudaEventDestroy(e);
@@ -677,16 +679,17 @@ static cudaError_t enqueue_kernels(sw_plan* p, cudaStream_t s, bool capturing) {
   // tails overlap.  Under capture the fork and join become graph edges.
   if (e == cudaSuccess) e = cudaEventRecord(p->fork, s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(p->side, p->fork, 0);
-  if (e == cudaSuccess) e = launch_pairs(32, p->pair_blocks32, p->db->view, p->params, p->state, p->scr, p->side);
-  if (e == cudaSuccess) e = launch_pairs(16, p->pair_blocks16, p->db->view, p->params, p->state, p->scr, s);
+  const int gc = p->gclass;
+  if (e == cudaSuccess) e = launch_pairs(32, gc, p->pair_blocks32, p->db->view, p->params, p->state, p->scr, p->side);
+  if (e == cudaSuccess) e = launch_pairs(16, gc, p->pair_blocks16, p->db->view, p->params, p->state, p->scr, s);
   if (p->opt.overlap_kernels) {
     // the inter-task kernel too, on a third stream and issued after the pair
     // kernels: one of its blocks needs a whole SM's registers, so it starts on
     // an SM when the pair blocks there run out of work, and no SM idles in
     // their tails
     if (e == cudaSuccess) e = cudaStreamWaitEvent(p->side2, p->fork, 0);
-    if (e == cudaSuccess) e = launch_inter(p->kc, p->db->view, p->params, p->state, p->scr, p->side2);
-    if (e == cudaSuccess) e = launch_inter2q(p->kc2, p->db->view, p->params, p->state, p->scr, p->side2);
+    if (e == cudaSuccess) e = launch_inter(p->kc, gc, p->db->view, p->params, p->state, p->scr, p->side2);
+    if (e == cudaSuccess) e = launch_inter2q(p->kc2, gc, p->db->view, p->params, p->state, p->scr, p->side2);
     if (e == cudaSuccess) e = record(p->ev[2], p->side2, capturing);
     if (e == cudaSuccess) e = cudaEventRecord(p->join2, p->side2);
   }
@@ -697,8 +700,8 @@ static cudaError_t enqueue_kernels(sw_plan* p, cudaStream_t s, bool capturing) {
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->join2, 0);
     if (e == cudaSuccess) e = record(p->ev_join, s, capturing);
   } else {
-    if (e == cudaSuccess) e = launch_inter(p->kc, p->db->view, p->params, p->state, p->scr, s);
-    if (e == cudaSuccess) e = launch_inter2q(p->kc2, p->db->view, p->params, p->state, p->scr, s);
+    if (e == cudaSuccess) e = launch_inter(p->kc, gc, p->db->view, p->params, p->state, p->scr, s);
+    if (e == cudaSuccess) e = launch_inter2q(p->kc2, gc, p->db->view, p->params, p->state, p->scr, s);
     if (e == cudaSuccess) e = record(p->ev[2], s, capturing);
   }
   if (e == cudaSuccess) e = launch_intra(p->ikc, p->db->view, p->params, p->state, p->scr, s);
@@ -708,7 +711,8 @@ static cudaError_t enqueue_kernels(sw_plan* p, cudaStream_t s, bool capturing) {
 
 static cudaError_t run_kernels(sw_plan* p, cudaStream_t s) {
   if (!p->opt.use_graph) return enqueue_kernels(p, s, false);
-  if (!p->graph) {
+  cudaGraphExec_t& graph = p->graphs[p->gclass];
+  if (!graph) {
     cudaStream_t cs;
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e != cudaSuccess) return e;
@@ -719,15 +723,15 @@ static cudaError_t run_kernels(sw_plan* p, cudaStream_t s) {
       e = cudaStreamEndCapture(cs, &g);
       if (e2 != cudaSuccess) e = e2;
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&p->graph, g, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&graph, g, 0);
     if (g) cudaGraphDestroy(g);
     cudaStreamDestroy(cs);
     if (e != cudaSuccess) {
-      p->graph = nullptr;
+      graph = nullptr;
       return e;
     }
   }
-  return cudaGraphLaunch(p->graph, s);
+  return cudaGraphLaunch(graph, s);
 }
 
 // Two queries per word (inter2q_kernel.cu): deals the batch's queries to
@@ -932,6 +936,7 @@ static sw_status plan_enqueue(sw_plan* p, const HostBatch& hb, int32_t nq, int32
   }
   CUDA_TRY(cudaMemcpyAsync(p->params, p->params_h, sizeof(SearchParams), cudaMemcpyHostToDevice, s));
   p->stream = s;
+  p->gclass = gap_class(P.go, P.ge);
   CUDA_TRY(run_kernels(p, s));
   CUDA_TRY(cudaMemcpyAsync(p->state_h, p->state, sizeof(SearchState), cudaMemcpyDeviceToHost, s));
   p->pending = sw_stats{};

@@ -133,6 +133,28 @@ __device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) {
   return r;
 }
 
+// The packed words of the gap penalties: GO2 = (Go, Go) (H' of H = 0),
+// NGE2 = (-Ge, -Ge) and MGO = -(Go, Go) as one 32-bit word.  Gap class G > 0
+// fixes them at compile time for a common setting, so they enter the
+// instructions as immediates instead of registers (on the paper-shaped search
+// the two-query kernel ran 6% faster so); G = 0 reads them from the
+// parameter block.  The classes are listed in swgb_internal.h (gap_class).
+template <int G>
+__device__ __forceinline__ void gap_words(const SearchParams* __restrict__ P, uint32_t& GO2,
+                                          uint32_t& NGE2, uint32_t& MGO) {
+  if constexpr (G == 0) {
+    const int go = P->go;
+    GO2 = pack2(go);
+    NGE2 = pack2(-P->ge);
+    MGO = (uint32_t)(-(int)((uint32_t)go * 65537u));
+  } else {
+    constexpr int go = GapClass<G>::GO, ge = GapClass<G>::GE;
+    GO2 = ((uint32_t)(uint16_t)go) * 0x00010001u;
+    NGE2 = ((uint32_t)(uint16_t)(int16_t)(-ge)) * 0x00010001u;
+    MGO = (uint32_t)(-(int)((uint32_t)go * 65537u));
+  }
+}
+
 // One packed cell update (Eq. 1-3, biased by +Go): returns H'; updates E' of
 // the next column in e and F' of the next row in f.
 __device__ __forceinline__ uint32_t packed_cell(uint32_t hd, uint32_t w, uint32_t& e, uint32_t& f,

@@ -153,7 +153,7 @@ __device__ __forceinline__ void q2_emit(const DbView& db, const SearchParams* __
   }
 }
 
-template <int T>
+template <int T, int G>
 __device__ void q2_item(const DbView& db, const SearchParams* __restrict__ P, SearchState* st,
                         const int8_t* __restrict__ sm, uint8_t* slice, int lane, int64_t warp_id,
                         const Scratch& scr, int k, int g, int h) {
@@ -163,10 +163,8 @@ __device__ void q2_item(const DbView& db, const SearchParams* __restrict__ P, Se
   // this lane's 8 residues of chunk c: bytes [8h, 8h + 8) of its 16-byte vector
   const uint2* __restrict__ res = (const uint2*)(db.inter + db.goff[g]) + lane * 2 + h;
   uint4* bd = scr.inter_border + warp_id * scr.inter_stride_vec + lane;
-  const int go = P->go;
-  const uint32_t GO2 = pack2(go);                                  // H' of H = 0
-  const uint32_t NGE2 = pack2(-P->ge);
-  const uint32_t MGO = (uint32_t)(-(int)((uint32_t)go * 65537u));  // - (Go, Go) as one word
+  uint32_t GO2, NGE2, MGO;  // (Go, Go), (-Ge, -Ge), -(Go, Go)
+  gap_words<G>(P, GO2, NGE2, MGO);
   const uint32_t one = (uint32_t)P->one;
   const int p16 = (lane & 7) * 16;
   const int nch = L / CHUNK;
@@ -275,7 +273,7 @@ __device__ void q2_item(const DbView& db, const SearchParams* __restrict__ P, Se
   }
 }
 
-template <int T>
+template <int T, int G>
 __global__ void __launch_bounds__(Q2Shape<T>::WARPS * 32, 1)
 inter2q_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scratch scr) {
   extern __shared__ __align__(16) uint8_t smem[];
@@ -295,17 +293,21 @@ inter2q_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, S
     if ((int64_t)it >= total) break;
     const int64_t gh = (int64_t)it / K;  // group halves, longest groups first
     const int k = (int)((int64_t)it - gh * K);
-    q2_item<T>(db, P, st, sm, slice, lane, warp_id, scr, k, P->g_first + (int)(gh >> 1),
-               (int)(gh & 1));
+    q2_item<T, G>(db, P, st, sm, slice, lane, warp_id, scr, k, P->g_first + (int)(gh >> 1),
+                  (int)(gh & 1));
   }
 }
 
 typedef void (*Inter2qKernel)(DbView, const SearchParams*, SearchState*, Scratch);
 
-static Inter2qKernel pick_inter2q(int rows) {
-  if (rows == 16) return inter2q_kernel<16>;
-  if (rows == 24) return inter2q_kernel<24>;
-  if (rows == 32) return inter2q_kernel<32>;
+// The default strip height (32 rows) is compiled for each gap class; 16
+// and 24 rows read the penalties at run time.
+static Inter2qKernel pick_inter2q(int rows, int gclass) {
+  if (rows == 16) return inter2q_kernel<16, 0>;
+  if (rows == 24) return inter2q_kernel<24, 0>;
+  if (rows == 32)
+    return gclass == 1 ? inter2q_kernel<32, 1> : gclass == 2 ? inter2q_kernel<32, 2>
+                                                             : inter2q_kernel<32, 0>;
   return nullptr;
 }
 
@@ -321,13 +323,15 @@ int inter2q_warps(int rows) {
 }
 
 int inter2q_blocks_per_sm(int rows, int warps) {
-  Inter2qKernel k = pick_inter2q(rows);
+  Inter2qKernel k = pick_inter2q(rows, 0);
   if (!k || warps < 1 || warps > inter2q_warps(rows)) return 0;
   const size_t smem = inter2q_smem_bytes(rows, warps);
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess) {
-    cudaGetLastError();
-    return 0;
+  for (int g = 0; g < GAP_CLASSES; g++) {  // every variant the plan may launch
+    if (cudaFuncSetAttribute(pick_inter2q(rows, g), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
   }
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, warps * 32, smem) != cudaSuccess) {
@@ -337,9 +341,10 @@ int inter2q_blocks_per_sm(int rows, int warps) {
   return nb;
 }
 
-cudaError_t launch_inter2q(const KernelConfig& kc, const DbView& db, const SearchParams* params,
-                           SearchState* state, const Scratch& scr, cudaStream_t stream) {
-  Inter2qKernel k = pick_inter2q(kc.variant);
+cudaError_t launch_inter2q(const KernelConfig& kc, int gclass, const DbView& db,
+                           const SearchParams* params, SearchState* state, const Scratch& scr,
+                           cudaStream_t stream) {
+  Inter2qKernel k = pick_inter2q(kc.variant, gclass);
   if (!k) return cudaErrorInvalidValue;
   k<<<kc.blocks, kc.warps * 32, kc.smem, stream>>>(db, params, state, scr);
   return cudaGetLastError();

@@ -188,7 +188,7 @@ __device__ __forceinline__ void packed_oct(uint32_t (&Hp)[T], uint32_t (&E)[T], 
   for (int q = 0; q < 4; q++) o[q] = make_uint4(bottom[2 * q], f[2 * q], bottom[2 * q + 1], f[2 * q + 1]);
 }
 
-template <int T, int WC>
+template <int T, int WC, int G>
 __device__ void inter_item(const DbView& db, const SearchParams* __restrict__ P, SearchState* st,
                            const int8_t* __restrict__ sm, uint8_t* slice, int lane,
                            int64_t warp_id, const Scratch& scr, int q, int g) {
@@ -198,9 +198,8 @@ __device__ void inter_item(const DbView& db, const SearchParams* __restrict__ P,
   const uint4* __restrict__ res = (const uint4*)(db.inter + db.goff[g]) + lane;
   uint4* bd = scr.inter_border + warp_id * scr.inter_stride_vec + lane;
   const int go = P->go;
-  const uint32_t GO2 = pack2(go);                                  // H' of H = 0
-  const uint32_t NGE2 = pack2(-P->ge);
-  const uint32_t MGO = (uint32_t)(-(int)((uint32_t)go * 65537u));  // - (Go, Go) as one word
+  uint32_t GO2, NGE2, MGO;  // (Go, Go), (-Ge, -Ge), -(Go, Go)
+  gap_words<G>(P, GO2, NGE2, MGO);
   const uint32_t ZERO2 = 0u;                                       // E' of E = -Go
   const uint32_t one = (uint32_t)P->one;
   const int p16 = (lane & 7) * 16;
@@ -331,7 +330,7 @@ __device__ void inter_item(const DbView& db, const SearchParams* __restrict__ P,
   }
 }
 
-template <int T, int WC>
+template <int T, int WC, int G>
 __global__ void __launch_bounds__(256, (T == 16 ? 2 : 1))
 inter_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scratch scr) {
   extern __shared__ __align__(16) uint8_t smem[];
@@ -351,16 +350,20 @@ inter_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scr
     if ((int64_t)it >= total) break;
     const int g = P->g_first + (int)((int64_t)it / nq);
     const int q = P->qorder[(int64_t)it % nq];
-    inter_item<T, WC>(db, P, st, sm, slice, lane, warp_id, scr, q, g);
+    inter_item<T, WC, G>(db, P, st, sm, slice, lane, warp_id, scr, q, g);
   }
 }
 
 typedef void (*InterKernel)(DbView, const SearchParams*, SearchState*, Scratch);
 
-static InterKernel pick_inter(int rows, int cols) {
-  if (rows == 16 && cols == 4) return inter_kernel<16, 4>;
-  if (rows == 32 && cols == 4) return inter_kernel<32, 4>;
-  if (rows == 32 && cols == 8) return inter_kernel<32, 8>;
+// The default shape (32 rows, eight columns) is compiled for each gap class;
+// the others read the penalties at run time.
+static InterKernel pick_inter(int rows, int cols, int gclass) {
+  if (rows == 16 && cols == 4) return inter_kernel<16, 4, 0>;
+  if (rows == 32 && cols == 4) return inter_kernel<32, 4, 0>;
+  if (rows == 32 && cols == 8)
+    return gclass == 1 ? inter_kernel<32, 8, 1> : gclass == 2 ? inter_kernel<32, 8, 2>
+                                                              : inter_kernel<32, 8, 0>;
   return nullptr;
 }
 
@@ -370,23 +373,25 @@ size_t inter_smem_bytes(int rows, int warps) {
 }
 
 int inter_blocks_per_sm(int rows, int cols, int warps) {
-  InterKernel k = pick_inter(rows, cols);
+  InterKernel k = pick_inter(rows, cols, 0);
   if (!k || warps < 1 || warps > 8) return 0;
   const size_t smem = inter_smem_bytes(rows, warps);
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess)
-    return 0;
+  for (int g = 0; g < GAP_CLASSES; g++)  // every variant the plan may launch
+    if (cudaFuncSetAttribute(pick_inter(rows, cols, g), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return 0;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, warps * 32, smem) != cudaSuccess)
     return 0;
   return nb;
 }
 
-cudaError_t launch_inter(const KernelConfig& kc, const DbView& db, const SearchParams* params,
-                         SearchState* state, const Scratch& scr, cudaStream_t stream) {
+cudaError_t launch_inter(const KernelConfig& kc, int gclass, const DbView& db,
+                         const SearchParams* params, SearchState* state, const Scratch& scr,
+                         cudaStream_t stream) {
   // the dynamic shared-memory attribute was set by inter_blocks_per_sm when
   // the plan was created; nothing here may be an unsafe call under capture
-  InterKernel k = pick_inter(kc.variant, kc.cols);
+  InterKernel k = pick_inter(kc.variant, kc.cols, gclass);
   if (!k) return cudaErrorInvalidValue;
   k<<<kc.blocks, kc.warps * 32, kc.smem, stream>>>(db, params, state, scr);
   return cudaGetLastError();

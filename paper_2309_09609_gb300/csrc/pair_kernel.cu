@@ -47,7 +47,7 @@ struct PairShape {
   static constexpr int MIN_BLOCKS = PR == 16 ? 4 : 2;  // 16 or 8 warps per SM
 };
 
-template <int PR>
+template <int PR, int G>
 __global__ void __launch_bounds__(PAIR_WARPS * 32, PairShape<PR>::MIN_BLOCKS)
 pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scratch scr) {
   constexpr int PQR = PairShape<PR>::PQR;
@@ -80,8 +80,8 @@ pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scra
   if (total <= 0) return;  // uniform over the grid
   unsigned long long* counter = PR == 32 ? &st->pair_work32 : &st->pair_work;
   const int go = P->go;
-  const uint32_t GO2 = pack2(go), NGE2 = pack2(-P->ge);
-  const uint32_t MGO = (uint32_t)(-(int)((uint32_t)go * 65537u));
+  uint32_t GO2, NGE2, MGO;  // (Go, Go), (-Ge, -Ge), -(Go, Go)
+  gap_words<G>(P, GO2, NGE2, MGO);
   const uint32_t one = (uint32_t)P->one;
   constexpr int ROWS = 32 * PR;
   for (;;) {
@@ -315,28 +315,37 @@ size_t pair_smem_bytes(int rows) {
   return (size_t)MATRIX_SMEM + (size_t)PAIR_WARPS * slice;
 }
 
+typedef void (*PairKernel)(DbView, const SearchParams*, SearchState*, Scratch);
+
+// Both widths are compiled for each gap class.
+static PairKernel pick_pair(int rows, int gclass) {
+  if (rows == 32)
+    return gclass == 1 ? pair_kernel<32, 1> : gclass == 2 ? pair_kernel<32, 2> : pair_kernel<32, 0>;
+  if (rows == 16)
+    return gclass == 1 ? pair_kernel<16, 1> : gclass == 2 ? pair_kernel<16, 2> : pair_kernel<16, 0>;
+  return nullptr;
+}
+
 int pair_blocks_per_sm(int rows) {
   if (rows != 16 && rows != 32) return 0;
-  void (*k)(DbView, const SearchParams*, SearchState*, Scratch) =
-      rows == 32 ? pair_kernel<32> : pair_kernel<16>;
+  PairKernel k = pick_pair(rows, 0);
   const size_t smem = pair_smem_bytes(rows);
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess)
-    return 0;
+  for (int g = 0; g < GAP_CLASSES; g++)  // every variant the plan may launch
+    if (cudaFuncSetAttribute(pick_pair(rows, g), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return 0;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, PAIR_WARPS * 32, smem) != cudaSuccess)
     return 0;
   return nb;
 }
 
-cudaError_t launch_pairs(int rows, int blocks, const DbView& db, const SearchParams* params,
-                         SearchState* state, const Scratch& scr, cudaStream_t stream) {
-  if (rows == 32)
-    pair_kernel<32><<<blocks, PAIR_WARPS * 32, pair_smem_bytes(32), stream>>>(db, params, state, scr);
-  else if (rows == 16)
-    pair_kernel<16><<<blocks, PAIR_WARPS * 32, pair_smem_bytes(16), stream>>>(db, params, state, scr);
-  else
-    return cudaErrorInvalidValue;
+cudaError_t launch_pairs(int rows, int gclass, int blocks, const DbView& db,
+                         const SearchParams* params, SearchState* state, const Scratch& scr,
+                         cudaStream_t stream) {
+  PairKernel k = pick_pair(rows, gclass);
+  if (!k) return cudaErrorInvalidValue;
+  k<<<blocks, PAIR_WARPS * 32, pair_smem_bytes(rows), stream>>>(db, params, state, scr);
   return cudaGetLastError();
 }
 

@@ -112,6 +112,22 @@ struct Scratch {
   int64_t pair_rows16;
 };
 
+// ---- gap classes ------------------------------------------------------------------
+// The packed kernels are compiled for two common gap settings with the
+// penalties as compile-time constants, besides the general form that reads
+// them at run time:
+//   class 1: gap_open 10, gap_extend 2 (Go = 12, Ge = 2), the paper's "10/2";
+//   class 2: gap_open 11, gap_extend 1 (Go = 12, Ge = 1), BLAST's default.
+template <int G> struct GapClass;
+template <> struct GapClass<1> { static constexpr int GO = 12, GE = 2; };
+template <> struct GapClass<2> { static constexpr int GO = 12, GE = 1; };
+constexpr int GAP_CLASSES = 3;
+inline int gap_class(int go, int ge) {
+  if (go == GapClass<1>::GO && ge == GapClass<1>::GE) return 1;
+  if (go == GapClass<2>::GO && ge == GapClass<2>::GE) return 2;
+  return 0;
+}
+
 // ---- kernel launchers -----------------------------------------------------------
 struct KernelConfig {
   int variant;     // inter: packed rows per thread (16/32); intra: int32 rows per lane (8/16)
@@ -124,16 +140,18 @@ struct KernelConfig {
 // Inter-task kernel, packed 16-bit (inter_kernel.cu).
 size_t inter_smem_bytes(int rows, int warps);
 int inter_blocks_per_sm(int rows, int cols, int warps);  // resident blocks per SM, 0 if none
-cudaError_t launch_inter(const KernelConfig& kc, const DbView& db, const SearchParams* params,
-                         SearchState* state, const Scratch& scr, cudaStream_t stream);
+cudaError_t launch_inter(const KernelConfig& kc, int gclass, const DbView& db,
+                         const SearchParams* params, SearchState* state, const Scratch& scr,
+                         cudaStream_t stream);
 
 // Inter-task kernel with two queries per word (inter2q_kernel.cu), 16, 24 or
 // 32 rows per strip.
 size_t inter2q_smem_bytes(int rows, int warps);
 int inter2q_warps(int rows);  // warps per block (one block per SM)
 int inter2q_blocks_per_sm(int rows, int warps);  // resident blocks per SM, 0 if none
-cudaError_t launch_inter2q(const KernelConfig& kc, const DbView& db, const SearchParams* params,
-                           SearchState* state, const Scratch& scr, cudaStream_t stream);
+cudaError_t launch_inter2q(const KernelConfig& kc, int gclass, const DbView& db,
+                           const SearchParams* params, SearchState* state, const Scratch& scr,
+                           cudaStream_t stream);
 
 // Int32 intra-task kernel (intra_kernel.cu): int32 items one warp each, then
 // flagged pairs one block each.  Scratch: one border row per warp.
@@ -154,8 +172,9 @@ cudaError_t launch_collect(int blocks, const DbView& db, const SearchParams* par
 constexpr int PAIR_WARPS = 4;  // warps per block
 int pair_blocks_per_sm(int rows);
 size_t pair_smem_bytes(int rows);
-cudaError_t launch_pairs(int rows, int blocks, const DbView& db, const SearchParams* params,
-                         SearchState* state, const Scratch& scr, cudaStream_t stream);
+cudaError_t launch_pairs(int rows, int gclass, int blocks, const DbView& db,
+                         const SearchParams* params, SearchState* state, const Scratch& scr,
+                         cudaStream_t stream);
 // pair_kernel<32> costs about 0.85 of pair_kernel<16> per cell it computes
 // but pads a query to 1024-row passes instead of 512: a query of m residues
 // goes to the wide kernel when 0.85 * ceil(m / 1024) * 1024 is below
