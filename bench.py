@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--rows", type=int, default=None, help="packed rows per thread (16/32)")
     ap.add_argument("--cutoff", type=int, default=None, help="inter/intra length cutoff")
+    ap.add_argument("--auto-cutoff", type=int, default=None, choices=[0, 1],
+                    help="plan option auto_cutoff (load balance of few-query searches)")
     ap.add_argument("--warps", type=int, default=None)
     ap.add_argument("--cols", type=int, default=None, help="inter-task wavefront columns (4/8)")
     ap.add_argument("--two-query", type=int, default=None, choices=[0, 1, 2],
@@ -357,6 +359,7 @@ def profiled_traffic(args, kernel="inter2q_kernel"):
                and getattr(args, "two_query", None) is None
                and getattr(args, "two_query_rows", None) is None
                and getattr(args, "two_query_pairs", None) is None
+               and getattr(args, "auto_cutoff", None) is None
                and getattr(args, "wide_min", None) is None
                and getattr(args, "wide_min_subject", None) is None)
     fname, srcs = TRAFFIC_RECORDS[key]
@@ -669,6 +672,8 @@ def run_native(args):
         opts["rows_per_thread"] = args.rows
     if args.cutoff is not None:
         opts["long_cutoff"] = args.cutoff
+    if args.auto_cutoff is not None:
+        opts["auto_cutoff"] = args.auto_cutoff
     if args.warps:
         opts["warps_per_block"] = args.warps
     if args.cols:

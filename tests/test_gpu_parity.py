@@ -133,14 +133,15 @@ def test_long_subjects_intra_task(intra_rows):
     assert_exact(res, oracle_all(q, db))
 
 
-def test_packed_pairs_odd_count_and_unequal_lengths():
+@pytest.mark.parametrize("gaps", [(10, 2), (11, 1), (6, 3)])   # the two gap classes, general
+def test_packed_pairs_odd_count_and_unequal_lengths(gaps):
     # 65 long subjects: the last pair has one subject; pairs of unequal length
     rng = np.random.default_rng(40)
     db = seqset(rng, list(rng.integers(200, 2000, size=65)) + [7, 0, 150])
     q = seqset(rng, [1, 100, 511, 512, 513, 1100])
-    res, st = all_paths(q, db, long_cutoff=100, plain=False)
+    res, st = all_paths(q, db, *gaps, long_cutoff=100, plain=False)
     assert st["intra_items"] >= 65 * len(q)
-    assert_exact(res, oracle_all(q, db))
+    assert_exact(res, oracle_all(q, db, *gaps))
 
 
 def test_pair_kernel_widths_split_the_queries():
@@ -361,16 +362,23 @@ def test_plan_reuse_across_batches_and_scoring():
     d = swgb.Database.from_seqset(db)
     p = d.plan(16, 8000, long_cutoff=800)
     m = rand_matrix(rng, -4, 6, symmetric=True)
+    # gap settings of every class the packed kernels are compiled for --
+    # (10, 2), (11, 1) and the general form -- alternate on one plan, which
+    # keeps a CUDA graph per class
     batches = [
         (seqset(rng, [100, 7, 300]), 10, 2, None),
         (seqset(rng, [45] * 9 + [512]), 3, 1, m),
         (seqset(rng, [1]), 10, 2, None),
         (seqset(rng, [0, 0]), 10, 2, None),
+        (seqset(rng, [250, 33, 700]), 11, 1, None),
+        (seqset(rng, [250, 33, 700]), 10, 2, m),
+        (seqset(rng, [250, 33, 700]), 9, 3, None),
+        (seqset(rng, [250, 33, 700]), 11, 1, None),
     ]
     for q, go, ge, mm in batches:
         got = p.search(q.res, q.lens, go, ge, mm)
         want = oracle_all(q, db, go, ge, None if mm is None else mm.astype(np.int32))
-        assert (got == want).all()
+        assert (got == want).all(), (go, ge)
 
 
 def test_async_search_and_bounded_wait():
