@@ -60,6 +60,31 @@ def test_options_default(lib):
     assert o.wide_min_len >= 0
 
 
+def test_options_struct_layout_matches_the_header(lib):
+    # every field of sw_options, as the library fills it in, at the offset
+    # the binding reads it from (a mismatched layout shifts these values)
+    o = swgb.options()
+    assert {k: getattr(o, k) for k, _ in swgb.Options._fields_} == {
+        "rows_per_thread": 32, "warps_per_block": 8, "long_cutoff": 1500, "intra_rows": 8,
+        "use_graph": 1, "force_int32": 0, "auto_cutoff": 0, "wide_min_len": 0,
+        "wide_min_subject": 4096, "inter_columns": 8, "overlap_kernels": 0, "two_query": 1,
+        "two_query_rows": 32, "two_query_pairs": 0, "flag_capacity": 0}
+    header = open(os.path.join(ROOT, "include", "swgb.h")).read()
+    body = re.search(r"typedef struct \{([^{}]*)\} sw_options;", header).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"int32_t\s+(\w+);", body)
+    assert fields == [k for k, _ in swgb.Options._fields_]
+
+
+def test_stats_struct_fields_match_the_header(lib):
+    header = open(os.path.join(ROOT, "include", "swgb.h")).read()
+    body = re.search(r"typedef struct \{([^{}]*)\} sw_stats;", header).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"(int32_t|int64_t|float)\s+(\w+);", body)
+    ctype = {"int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "float": ctypes.c_float}
+    assert [(n, ctype[t]) for t, n in fields] == list(swgb.Stats._fields_)
+
+
 def test_db_create_rejects_bad_input_before_touching_the_gpu(lib):
     with pytest.raises(swgb.SwError) as e:
         swgb.Database(np.array([0, 1, 30], np.uint8), np.array([3], np.int32))
