@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--rows", type=int, default=None, help="packed rows per thread (16/32)")
     ap.add_argument("--cutoff", type=int, default=None, help="inter/intra length cutoff")
+    ap.add_argument("--overlap", type=int, default=None, choices=[0, 1],
+                    help="plan option overlap_kernels (inter-task kernels beside the pair kernels)")
     ap.add_argument("--auto-cutoff", type=int, default=None, choices=[0, 1],
                     help="plan option auto_cutoff (load balance of few-query searches)")
     ap.add_argument("--warps", type=int, default=None)
@@ -360,6 +362,7 @@ def profiled_traffic(args, kernel="inter2q_kernel"):
                and getattr(args, "two_query_rows", None) is None
                and getattr(args, "two_query_pairs", None) is None
                and getattr(args, "auto_cutoff", None) is None
+               and getattr(args, "overlap", None) is None
                and getattr(args, "wide_min", None) is None
                and getattr(args, "wide_min_subject", None) is None)
     fname, srcs = TRAFFIC_RECORDS[key]
@@ -674,6 +677,8 @@ def run_native(args):
         opts["long_cutoff"] = args.cutoff
     if args.auto_cutoff is not None:
         opts["auto_cutoff"] = args.auto_cutoff
+    if args.overlap is not None:
+        opts["overlap_kernels"] = args.overlap
     if args.warps:
         opts["warps_per_block"] = args.warps
     if args.cols:

@@ -362,15 +362,18 @@ cudaError_t launch_align(const DbView& db, const SearchParams* params, const Ali
     e = cudaFuncSetAttribute(align_forward_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
+    cudaGetLastError();  // a stale error must not be read as this launch's
     align_forward_block<<<std::min(n_items, std::max(sms, 1)), ABW * 32, smem, stream>>>(
         db, params, items, n_items, bits, border, out);
   } else {
     const int blocks = std::min((n_items + ALIGN_WARPS - 1) / ALIGN_WARPS, std::max(sms, 1) * 8);
+    cudaGetLastError();  // a stale error must not be read as this launch's
     align_forward<<<blocks, ALIGN_WARPS * 32, 0, stream>>>(db, params, items, n_items, bits,
                                                            border, out);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  cudaGetLastError();  // a stale error must not be read as this launch's
   align_traceback<<<(n_items + 127) / 128, 128, 0, stream>>>(db, params, items, n_items, bits, out,
                                                              ops);
   return cudaGetLastError();

@@ -212,6 +212,7 @@ static void db_free(sw_db* db) {
   cudaFree(db->clen);
   cudaFree(db->perm);
   cudaSetDevice(cur);
+  cudaGetLastError();  // a failed free or device switch leaves no stale error
   delete db;
 }
 
@@ -414,6 +415,7 @@ static sw_status fill_scoring(SearchParams& P, int32_t gap_open, int32_t gap_ext
 // ---- plan ---------------------------------------------------------------------------------
 struct sw_plan {
   sw_db* db = nullptr;
+  int device = 0;           // the database's device, kept for plan_free
   sw_options opt{};
   KernelConfig kc{};        // inter-task kernel
   KernelConfig kc2{};       // inter-task kernel, two queries per word
@@ -467,7 +469,9 @@ static void plan_free(sw_plan* p) {
   if (!p) return;
   int cur = 0;
   cudaGetDevice(&cur);
-  if (p->db) cudaSetDevice(p->db->device);
+  // the plan's own device: its database may already be gone (a garbage
+  // collector can finalize the two in either order)
+  cudaSetDevice(p->device);
   for (auto& g : p->graphs)
     if (g) cudaGraphExecDestroy(g);
   if (p->done) cudaEventDestroy(p->done);
@@ -501,6 +505,7 @@ static void plan_free(sw_plan* p) {
   cudaFreeHost(p->strips_h);
   cudaFreeHost(p->spairs_h);
   cudaSetDevice(cur);
+  cudaGetLastError();  // a failed free or device switch leaves no stale error
   delete p;
 }
 
@@ -535,6 +540,7 @@ extern "C" sw_status sw_plan_create(sw_db* db, int32_t max_queries, int64_t max_
 
   sw_plan* p = new sw_plan();
   p->db = db;
+  p->device = db->device;
   p->opt = o;
   p->max_queries = max_queries;
   p->max_residues = max_query_residues;

@@ -156,14 +156,25 @@ __device__ __forceinline__ void gap_words(const SearchParams* __restrict__ P, ui
 }
 
 // One packed cell update (Eq. 1-3, biased by +Go): returns H'; updates E' of
-// the next column in e and F' of the next row in f.
+// the next column in e and F' of the next row in f.  H' - Go goes to the FMA
+// pipe either way: with compile-time penalties (G > 0) as a 16x2 subtract of
+// the immediate (Go, Go), otherwise as one 32-bit IMAD by the run-time
+// register `one` (no borrow crosses the halves, since H' >= Go in each).  On
+// the paper-shaped search the subtract took the two-query kernel from 826 to
+// 801 ms with compile-time penalties, and from 881 to 898 ms with run-time
+// ones.
+template <int G>
 __device__ __forceinline__ uint32_t packed_cell(uint32_t hd, uint32_t w, uint32_t& e, uint32_t& f,
                                                 uint32_t GO2, uint32_t NGE2, uint32_t MGO,
                                                 uint32_t one) {
   const uint32_t h = __viaddmax_s16x2(hd, w, __vimax3_s16x2(e, f, GO2));  // H'
-  const uint32_t t = imad(h, one, MGO);  // H' - Go in both halves (FMA pipe)
-  e = __viaddmax_s16x2(e, NGE2, t);      // E' of the next column
-  f = __viaddmax_s16x2(f, NGE2, t);      // F' of the next row
+  uint32_t t;                                                              // H' - Go
+  if constexpr (G > 0)
+    t = __vsub2(h, GO2);
+  else
+    t = imad(h, one, MGO);
+  e = __viaddmax_s16x2(e, NGE2, t);  // E' of the next column
+  f = __viaddmax_s16x2(f, NGE2, t);  // F' of the next row
   return h;
 }
 

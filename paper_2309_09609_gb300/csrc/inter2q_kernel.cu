@@ -69,7 +69,7 @@ __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) 
 // the bottom of the strip.  A chunk runs as two wavefronts of four columns:
 // on the paper-shaped search that was 3% faster than one of eight (880
 // against 907 ms at 32 rows) and no slower than four of two.
-template <int T, int W, int C0>
+template <int T, int W, int C0, int G>
 __device__ __forceinline__ void q2_wave(uint32_t (&Hp)[T], uint32_t (&E)[T], uint32_t& hdiag,
                                        uint32_t& smax, const uint8_t* prof, int p16, const uint2 rr,
                                        const uint4* b, uint4* o, uint32_t GO2,
@@ -114,7 +114,7 @@ __device__ __forceinline__ void q2_wave(uint32_t (&Hp)[T], uint32_t (&E)[T], uin
         hd = r == 0 ? htop[c - 1] : last2[c - 1];  // H' of column c - 1, row r - 1
       }
       uint32_t e = E[r];
-      out[c] = packed_cell(hd, w, e, f[c], GO2, NGE2, MGO, one);
+      out[c] = packed_cell<G>(hd, w, e, f[c], GO2, NGE2, MGO, one);
       E[r] = e;
       if (c == W - 1) Hp[r] = out[c];
       if (r == T - 1) bottom[c] = out[c];
@@ -245,8 +245,8 @@ __device__ void q2_item(const DbView& db, const SearchParams* __restrict__ P, Se
       const uint4 bv[4] = {bring[(slot * 4 + 0) * 32], bring[(slot * 4 + 1) * 32],
                            bring[(slot * 4 + 2) * 32], bring[(slot * 4 + 3) * 32]};
       uint4 ov[4];
-      q2_wave<T, 4, 0>(Hp, E, hdiag, smax, slice, p16, rr, bv, ov, GO2, NGE2, MGO, one);
-      q2_wave<T, 4, 4>(Hp, E, hdiag, smax, slice, p16, rr, bv + 2, ov + 2, GO2, NGE2, MGO, one);
+      q2_wave<T, 4, 0, G>(Hp, E, hdiag, smax, slice, p16, rr, bv, ov, GO2, NGE2, MGO, one);
+      q2_wave<T, 4, 4, G>(Hp, E, hdiag, smax, slice, p16, rr, bv + 2, ov + 2, GO2, NGE2, MGO, one);
       if (!last) {
         if (keep != 0xffffffffu) {  // uniform: some query ends in this strip
 #pragma unroll
@@ -346,6 +346,7 @@ cudaError_t launch_inter2q(const KernelConfig& kc, int gclass, const DbView& db,
                            cudaStream_t stream) {
   Inter2qKernel k = pick_inter2q(kc.variant, gclass);
   if (!k) return cudaErrorInvalidValue;
+  cudaGetLastError();  // a stale error must not be read as this launch's
   k<<<kc.blocks, kc.warps * 32, kc.smem, stream>>>(db, params, state, scr);
   return cudaGetLastError();
 }

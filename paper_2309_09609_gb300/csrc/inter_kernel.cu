@@ -48,7 +48,7 @@ __device__ __forceinline__ uint32_t profile_word(const uint4 (&va)[T / 16], cons
 // of the previous column on entry and of the fourth column on exit; b0, b1
 // are the border vectors (H'_c, F'_c) above the strip for columns 0,1 and 2,3;
 // o0, o1 receive the strip's bottom row in the same layout.
-template <int T>
+template <int T, int G>
 __device__ __forceinline__ void packed_quad(uint32_t (&Hp)[T], uint32_t (&E)[T], uint32_t& hdiag,
                                             uint32_t& smax, const uint8_t* slice, int p16,
                                             uint32_t wa, uint32_t wb, const uint4& b0,
@@ -87,7 +87,7 @@ __device__ __forceinline__ void packed_quad(uint32_t (&Hp)[T], uint32_t (&E)[T],
         hd = r == 0 ? htop[c - 1] : last2[c - 1];  // H' of column c - 1, row r - 1
       }
       uint32_t e = E[r];
-      out[c] = packed_cell(hd, profile_word<T>(pa[c], pb[c], r), e, f[c], GO2, NGE2, MGO, one);
+      out[c] = packed_cell<G>(hd, profile_word<T>(pa[c], pb[c], r), e, f[c], GO2, NGE2, MGO, one);
       E[r] = e;
       if (c == W - 1) Hp[r] = out[c];
       if (r == T - 1) bottom[c] = out[c];
@@ -115,7 +115,7 @@ __device__ __forceinline__ void packed_quad(uint32_t (&Hp)[T], uint32_t (&E)[T],
 // loaded when the column reaches row 0 and row 16, so eight columns take the
 // profile registers of four.  b[q] / o[q] hold (H'_c, F'_c) of columns 2q and
 // 2q + 1 above / at the bottom of the strip.
-template <int T>
+template <int T, int G>
 __device__ __forceinline__ void packed_oct(uint32_t (&Hp)[T], uint32_t (&E)[T], uint32_t& hdiag,
                                            uint32_t& smax, const uint8_t* slice, int p16,
                                            const uint4& rr, const uint4 (&b)[4], uint4 (&o)[4],
@@ -167,7 +167,7 @@ __device__ __forceinline__ void packed_oct(uint32_t (&Hp)[T], uint32_t (&E)[T], 
       const uint32_t a32 = wq == 0 ? pa[c].x : wq == 1 ? pa[c].y : wq == 2 ? pa[c].z : pa[c].w;
       const uint32_t b32 = wq == 0 ? pb[c].x : wq == 1 ? pb[c].y : wq == 2 ? pb[c].z : pb[c].w;
       uint32_t e = E[r];
-      out[c] = packed_cell(hd, prmt(a32, b32, sext_pair_sel(r & 3)), e, f[c], GO2, NGE2, MGO, one);
+      out[c] = packed_cell<G>(hd, prmt(a32, b32, sext_pair_sel(r & 3)), e, f[c], GO2, NGE2, MGO, one);
       E[r] = e;
       if (c == W - 1) Hp[r] = out[c];
       if (r == T - 1) bottom[c] = out[c];
@@ -277,7 +277,7 @@ __device__ void inter_item(const DbView& db, const SearchParams* __restrict__ P,
         const uint4 bv[4] = {bring[(slot * 4 + 0) * 32], bring[(slot * 4 + 1) * 32],
                              bring[(slot * 4 + 2) * 32], bring[(slot * 4 + 3) * 32]};
         uint4 ov[4];
-        packed_oct<T>(Hp, E, hdiag, smax, slice, p16, rr, bv, ov, GO2, NGE2, MGO, one);
+        packed_oct<T, G>(Hp, E, hdiag, smax, slice, p16, rr, bv, ov, GO2, NGE2, MGO, one);
         if (!last) {
 #pragma unroll
           for (int q = 0; q < 4; q++) bd[(c * 4 + q) * 32] = ov[q];
@@ -293,7 +293,7 @@ __device__ void inter_item(const DbView& db, const SearchParams* __restrict__ P,
         const uint4 b0 = bring[(slot * 4 + 2 * hq) * 32];
         const uint4 b1 = bring[(slot * 4 + 2 * hq + 1) * 32];
         uint4 o0, o1;
-        packed_quad<T>(Hp, E, hdiag, smax, slice, p16, wa, wb, b0, b1, o0, o1, GO2, NGE2, MGO,
+        packed_quad<T, G>(Hp, E, hdiag, smax, slice, p16, wa, wb, b0, b1, o0, o1, GO2, NGE2, MGO,
                        one);
         if (!last) {
           bd[(c * 4 + 2 * hq) * 32] = o0;
@@ -393,6 +393,7 @@ cudaError_t launch_inter(const KernelConfig& kc, int gclass, const DbView& db,
   // the plan was created; nothing here may be an unsafe call under capture
   InterKernel k = pick_inter(kc.variant, kc.cols, gclass);
   if (!k) return cudaErrorInvalidValue;
+  cudaGetLastError();  // a stale error must not be read as this launch's
   k<<<kc.blocks, kc.warps * 32, kc.smem, stream>>>(db, params, state, scr);
   return cudaGetLastError();
 }

@@ -275,6 +275,7 @@ __global__ void collect_kernel(DbView db, const SearchParams* __restrict__ P, Se
 
 cudaError_t launch_collect(int blocks, const DbView& db, const SearchParams* params,
                            SearchState* state, const Scratch& scr, cudaStream_t stream) {
+  cudaGetLastError();  // a stale error must not be read as this launch's
   collect_kernel<<<blocks, 256, 0, stream>>>(db, params, state, scr);
   return cudaGetLastError();
 }
@@ -310,6 +311,7 @@ cudaError_t launch_intra(const KernelConfig& kc, const DbView& db, const SearchP
                          SearchState* state, const Scratch& scr, cudaStream_t stream) {
   IntraKernel k = pick_intra(kc.variant);
   if (!k) return cudaErrorInvalidValue;
+  cudaGetLastError();  // a stale error must not be read as this launch's
   k<<<kc.blocks, INTRA_WARPS * 32, kc.smem, stream>>>(db, params, state, scr);
   return cudaGetLastError();
 }

@@ -232,7 +232,7 @@ pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scra
             for (int i = 0; i < PQR; i++) {
               const int r = k * PQR + i;
               uint32_t e = E[r];
-              const uint32_t h = packed_cell(hd, prmt(wa[k][i >> 2], wb[k][i >> 2],
+              const uint32_t h = packed_cell<G>(hd, prmt(wa[k][i >> 2], wb[k][i >> 2],
                                                       sext_pair_sel(i & 3)), e, f, GO2, NGE2, MGO, one);
               hd = Hp[r];
               Hp[r] = h;
@@ -345,6 +345,7 @@ cudaError_t launch_pairs(int rows, int gclass, int blocks, const DbView& db,
                          cudaStream_t stream) {
   PairKernel k = pick_pair(rows, gclass);
   if (!k) return cudaErrorInvalidValue;
+  cudaGetLastError();  // a stale error must not be read as this launch's
   k<<<blocks, PAIR_WARPS * 32, pair_smem_bytes(rows), stream>>>(db, params, state, scr);
   return cudaGetLastError();
 }

@@ -89,6 +89,7 @@ int plain_blocks_per_sm() {
 
 cudaError_t launch_plain(int blocks, const DbView& db, const SearchParams* params, int query,
                          int2* border, const int64_t* border_off, cudaStream_t stream) {
+  cudaGetLastError();  // a stale error must not be read as this launch's
   plain_kernel<<<blocks, GROUP, 0, stream>>>(db, params, query, border, border_off);
   return cudaGetLastError();
 }

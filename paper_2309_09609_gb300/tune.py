@@ -3,8 +3,10 @@
 The options (all of which change speed only, never a score):
 
 * two queries per word in the inter-task kernel (``two_query``: by the
-  plan's cost model, or never) and that kernel's strip height (32, 24, 16
-  rows);
+  plan's cost model, or never); its strip height stays at 32 rows, the only
+  height compiled with the gap penalties as constants (on the batched
+  workload a tuner that tried 24 rows on its 8-query sample picked them, and
+  the full batch then ran 7% slower);
 * the one-query inter-task kernel's rows per thread (32, 16), columns per
   wavefront with 32 rows (8, 4) and warps per block (8, 4);
 * the inter/intra length cutoff (1500, 3000, 7000, none) and the rows per
@@ -57,7 +59,6 @@ def space(db, n_queries: int) -> dict:
     sp = {}
     if n_queries >= 2:
         sp["two_query"] = [1, 0]
-        sp["two_query_rows"] = [32, 24, 16]
     sp["rows_per_thread"] = [32, 16]
     sp["inter_columns"] = [8, 4]
     sp["warps_per_block"] = [8, 4]

@@ -6,7 +6,9 @@ DPX add is ``add.s16x2``, without saturation).  The claim: a pair's 16-bit
 score is exact unless S' >= 32767 - max(SM), and exactly the pairs whose true
 biased score reaches that threshold are flagged for the int32 recompute.
 Overflow in one half never reaches the other, because h' >= Go in both
-halves, so the word-wide subtraction of (Go, Go) never borrows.
+halves, so the word-wide subtraction of (Go, Go) never borrows; the kernels
+compiled for a fixed gap setting subtract (Go, Go) half by half instead,
+which cannot cross halves at all, and both forms are modelled.
 
 ``packed_model`` below restates that arithmetic step by step (Eq. 1-3 with
 the bias), independently of the CUDA sources; the oracle gives the exact
@@ -26,11 +28,12 @@ def wrap16(x):
     return ((x + 32768) & 0xFFFF) - 32768
 
 
-def packed_model(qs, ds, gap_open, gap_extend, sm):
+def packed_model(qs, ds, gap_open, gap_extend, sm, h_minus_go="word"):
     """16-bit biased scores and flags of pairs (qs[k], ds[k]), two per word.
 
-    All queries share one length and all subjects another.  Returns
-    (S' per pair, flagged per pair)."""
+    All queries share one length and all subjects another.  h' - Go is one
+    32-bit subtraction of the packed word ("word") or a wrapping 16-bit
+    subtraction per half ("half").  Returns (S' per pair, flagged per pair)."""
     B = len(qs)
     assert B % 2 == 0
     m, n = len(qs[0]), len(ds[0])
@@ -48,6 +51,11 @@ def packed_model(qs, ds, gap_open, gap_extend, sm):
         t[1::2] = wrap16((word >> 16) & 0xFFFF)
         return t
 
+    def sub_go_half(h):
+        return wrap16(h - Go)
+
+    sub_go = sub_go_word if h_minus_go == "word" else sub_go_half
+
     h_up = np.full((B, n + 1), Go, np.int64)     # H' of the row above (row 0: H = 0)
     f_dn = np.zeros((B, n + 1), np.int64)        # F' entering this row (row 1: F = -Go)
     S = np.full(B, Go, np.int64)                 # S' (S = 0)
@@ -61,7 +69,7 @@ def packed_model(qs, ds, gap_open, gap_extend, sm):
             f = f_dn[:, j]
             h = np.maximum(wrap16(h_up[:, j - 1] + w_row[:, j - 1]),
                            np.maximum(np.maximum(e, f), Go))          # Eq. 1
-            t = sub_go_word(h)
+            t = sub_go(h)
             e = np.maximum(wrap16(e - Ge), t)                          # Eq. 2
             f_next[:, j] = np.maximum(wrap16(f - Ge), t)               # Eq. 3
             h_row[:, j] = h
@@ -102,12 +110,13 @@ def exact(qs, ds, gap_open, gap_extend, sm):
     return np.array([oracle.sw_score(q, d, gap_open, gap_extend, sm) for q, d in zip(qs, ds)])
 
 
-@pytest.mark.parametrize("seed,gaps", [(0, (10, 2)), (1, (40, 9)), (2, (0, 1))])
-def test_flags_exactly_the_pairs_at_the_threshold_and_the_rest_is_exact(seed, gaps):
+@pytest.mark.parametrize("h_minus_go", ["word", "half"])
+@pytest.mark.parametrize("seed,gaps", [(0, (10, 2)), (1, (40, 9)), (2, (0, 1)), (3, (11, 1))])
+def test_flags_exactly_the_pairs_at_the_threshold_and_the_rest_is_exact(seed, gaps, h_minus_go):
     rng = np.random.default_rng(300 + seed)
     sm = heavy_matrix(rng)
     qs, ds = pairs_near_the_limit(rng, 16, 330, 360, sm)
-    Sp, flagged = packed_model(qs, ds, *gaps, sm)
+    Sp, flagged = packed_model(qs, ds, *gaps, sm, h_minus_go)
     S = exact(qs, ds, *gaps, sm)
     Go = gaps[0] + gaps[1]
     thr = LIMIT - int(sm.max())
