@@ -140,7 +140,8 @@ void sw_options_default(sw_options* opt);
 /* Statistics of the last search run through a plan. */
 typedef struct {
   int64_t cells;             /* sum(query lengths) * sum(subject lengths) */
-  int64_t inter_items;       /* (query, group of 64 subjects) work items */
+  int64_t inter_items;       /* (query, group of 64 subjects) work items of the two-subject
+                                inter-task kernel (0 when the two-query kernel ran) */
   int64_t intra_items;       /* (query, long subject) work items */
   int64_t recomputed_pairs;  /* pairs whose 16-bit score saturated, redone in int32 */
   int32_t overflow_rounds;   /* extra rounds of the int32 kernel that the last search ran
@@ -176,18 +177,25 @@ sw_status sw_plan_create(sw_db* db, int32_t max_queries, int64_t max_query_resid
 void sw_plan_destroy(sw_plan* plan);
 
 /* Exact scores of every query against every subject (Eq. 1-3), the batched
- * path: four persistent launches, each taking its work longest first from
+ * path: five persistent launches, each taking its work longest first from
  * its own atomic counter -- the packed intra-task kernel over (pair of
  * subjects longer than opt.long_cutoff, query) items, at 32 and at 16 query
  * rows per lane, the two launches side by side on two streams (opt.
  * wide_min_len and opt.wide_min_subject split the items between them); then
- * the packed inter-task kernel over (query, group of 64 subjects) items --
- * all three scoring two subjects per 32-bit word in 16 bits -- and last the
- * int32 intra-task kernel, which recomputes every pair whose 16-bit score may
- * have saturated (one block per pair).  With gap penalties too large for 16
- * bits, or opt.force_int32, every pair goes to the int32 kernel instead (one
- * warp per pair).  The launch sequence is replayed from a CUDA graph when
- * opt.use_graph is set.
+ * one of the two packed inter-task kernels for the other subjects: two
+ * queries per 32-bit word against one subject per lane, over (pair of query
+ * streams, half of a group of 64 subjects) items, or two subjects per word,
+ * over (query, group of 64 subjects) items (opt.two_query and a cost model
+ * choose per search; a single query always takes the latter; the other
+ * kernel finds no items); and last the int32 intra-task kernel, which
+ * recomputes every pair whose 16-bit score may have saturated (one block per
+ * pair; more saturated pairs than opt.flag_capacity are recomputed in further
+ * rounds before the call returns).  With gap penalties too large for 16 bits,
+ * or opt.force_int32, every pair goes to the int32 kernel instead (one warp
+ * per pair).  The packed kernels are compiled with the gap penalties as
+ * constants for (10, 2) and (11, 1), and read them at run time otherwise.
+ * The launch sequence is replayed from a CUDA graph (one per such gap
+ * setting) when opt.use_graph is set.
  *   queries:   concatenated query codes (sum(q_lengths) bytes), host or device.
  *   q_lengths: n_queries int32, host or device.
  *   scores:    n_queries x n_subjects int32, host or device, written in full.

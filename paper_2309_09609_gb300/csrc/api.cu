@@ -4,11 +4,15 @@
 //     layouts (interleaved groups of 64 for the inter-task kernel, contiguous
 //     for the intra-task kernel); the split of the database by length into a
 //     short (inter-task) and long (intra-task) part follows Section III-A.
-//   * sw_plan_*: a reusable search context.  All device memory is allocated
-//     once; per search only the query block and a parameter block are copied,
-//     and the kernel sequence (reset counters; the two pair-kernel widths on
-//     two streams; the inter-task kernel; the int32 kernel for saturated
-//     pairs) is replayed from one CUDA graph.
+//   * sw_plan_*: a reusable search context.  Its device memory is allocated
+//     once (the host-order scores buffer at the first search that needs it);
+//     per search only the query block, the query-stream strip table and a
+//     parameter block are copied, and the kernel sequence (reset counters;
+//     the two pair-kernel widths on two streams; the two inter-task kernels,
+//     of which the plan gives one the items; the int32 kernel for saturated
+//     pairs) is replayed from a CUDA graph, one per gap class.  A flag-list
+//     overflow is recomputed in further rounds after the graph.
+//   * sw_search: through a plan kept by the database.
 //   * sw_search_plain: the int32 baseline, one kernel launch per query.
 //   * sw_align: optimal alignments with traceback of selected pairs.
 #include <algorithm>
