@@ -181,9 +181,17 @@ pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scra
         if constexpr (PR == 32) {
           // lane 0's top border, column t, from the previous pass (unused on
           // the first): every lane loads the same (clamped, so in bounds)
-          // word, so the load is one broadcast and no lane branches
-          const uint2 bv = hb[min(t, n0 - 1)];
-          const bool from_scratch = p > 0 && t < n0;
+          // word, so the load is one broadcast and no lane branches; in the
+          // steady state t < n0 holds, so neither clamp nor test is needed
+          uint2 bv;
+          bool from_scratch;
+          if constexpr (CHECK) {
+            bv = hb[min(t, n0 - 1)];
+            from_scratch = p > 0 && t < n0;
+          } else {
+            bv = hb[t];
+            from_scratch = p > 0;
+          }
           if (lane == 0) {
             in_h = from_scratch ? bv.x : GO2;  // else H(0, j) = 0
             in_f = from_scratch ? bv.y : 0u;   // else F(1, j) = -Go
