@@ -128,6 +128,12 @@ pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scra
       if constexpr (PR == 32)
         lane_profile<16>(prof + PHALF, sm, qr, m, p * ROWS + lane * PR + 16, lane);
       load_block(0);
+      if constexpr (PR == 32) {
+        // the row above the matrix, for the first pass's steady-state steps
+        // (lane 0 reads column j at step j; lane 31 rewrites it 127 steps later)
+        if (p == 0)
+          for (int j = lane; j < n0; j += 32) hb[j] = make_uint2(GO2, 0u);
+      }
       __syncwarp();
       uint32_t Hp[PR], E[PR];
 #pragma unroll
@@ -183,18 +189,21 @@ pair_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Scra
           // the first): every lane loads the same (clamped, so in bounds)
           // word, so the load is one broadcast and no lane branches; in the
           // steady state t < n0 holds, so neither clamp nor test is needed
-          uint2 bv;
-          bool from_scratch;
           if constexpr (CHECK) {
-            bv = hb[min(t, n0 - 1)];
-            from_scratch = p > 0 && t < n0;
+            const uint2 bv = hb[min(t, n0 - 1)];
+            const bool from_scratch = p > 0 && t < n0;
+            if (lane == 0) {
+              in_h = from_scratch ? bv.x : GO2;  // else H(0, j) = 0
+              in_f = from_scratch ? bv.y : 0u;   // else F(1, j) = -Go
+            }
           } else {
-            bv = hb[t];
-            from_scratch = p > 0;
-          }
-          if (lane == 0) {
-            in_h = from_scratch ? bv.x : GO2;  // else H(0, j) = 0
-            in_f = from_scratch ? bv.y : 0u;   // else F(1, j) = -Go
+            // the first pass's row holds (H', F') = (Go, 0) here (filled
+            // before the pass), so the value needs no test either
+            const uint2 bv = hb[t];
+            if (lane == 0) {
+              in_h = bv.x;
+              in_f = bv.y;
+            }
           }
         } else if (lane == 0) {
           if (p > 0 && c0 < n0) {
