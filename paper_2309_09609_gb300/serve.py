@@ -102,8 +102,12 @@ class _Slot:
         with torch.cuda.stream(self.stream):   # allocated for use on this stream
             self.scores = torch.empty((lengths.size, self.n), dtype=torch.int32,
                                       device=f"cuda:{self.device}")
-        self.plan.search_async(queries, lengths, self.scores, gap_open, gap_extend, matrix,
-                               stream=self.stream)
+        try:
+            self.plan.search_async(queries, lengths, self.scores, gap_open, gap_extend, matrix,
+                                   stream=self.stream)
+        except Exception:
+            self.scores = None                   # nothing was queued: release the rows
+            raise
 
     def poll(self) -> bool:
         """True once the batch's scores are complete (raises if it failed)."""
