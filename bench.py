@@ -78,7 +78,9 @@ def parse():
                     help="two queries per word in the inter-task kernel: 0 never, 1 auto, 2 always")
     ap.add_argument("--two-query-rows", type=int, default=None, choices=[16, 24, 32])
     ap.add_argument("--two-query-pairs", type=int, default=None,
-                    help="stream pairs of the two-query kernel (default: the plan's choice)")
+                    help="stream pairs of the two-query kernels (default: the plan's choice)")
+    ap.add_argument("--two-query-long", type=int, default=None, choices=[0, 1, 2],
+                    help="two queries per word against long subjects: 0 never, 1 auto, 2 always")
     ap.add_argument("--wide-min", type=int, default=None,
                     help="shortest query scored 32 rows per lane against long subjects")
     ap.add_argument("--wide-min-subject", type=int, default=None,
@@ -322,6 +324,8 @@ TRAFFIC_RECORDS = {
                                          ("inter2q_kernel.cu", "device_common.cuh")),
     ("pair_kernel", "long"): ("pair_kernel_long-sequences_traffic.txt",
                               ("pair_kernel.cu", "device_common.cuh")),
+    ("pair2q_kernel", "long"): ("pair2q_kernel_long-sequences_traffic.txt",
+                                ("pair2q_kernel.cu", "device_common.cuh")),
 }
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", TRAFFIC_RECORDS[("inter2q_kernel", "paper-search")][0])
 KERNEL_SOURCES = [os.path.join(CSRC, f) for f in TRAFFIC_RECORDS[("inter2q_kernel", "paper-search")][1]]
@@ -361,6 +365,7 @@ def profiled_traffic(args, kernel="inter2q_kernel"):
                and getattr(args, "two_query", None) is None
                and getattr(args, "two_query_rows", None) is None
                and getattr(args, "two_query_pairs", None) is None
+               and getattr(args, "two_query_long", None) is None
                and getattr(args, "auto_cutoff", None) is None
                and getattr(args, "overlap", None) is None
                and getattr(args, "wide_min", None) is None
@@ -470,13 +475,16 @@ def roofline(t, peak, peak_source, rate_mhz, traffic):
     stats = t["stats"]
     per_kernel = {}
     two_q = stats.get("inter2_items", 0) > 0
+    two_q_long = stats.get("pair2_items", 0) > 0
     inter_name = ("inter2q_kernel (packed inter-task, two queries per word)" if two_q
                   else "inter_kernel (packed inter-task)")
+    pair_name = ("pair2q_kernel (packed intra-task, two queries per word)" if two_q_long
+                 else "pair_kernel (packed intra-task)")
     for name, kcells, kms_list, ops in (
             (inter_name, stats["inter_cells"], t["kernel_ms"],
              TWO_QUERY_ALU_OPS_PER_CELL if two_q else PACKED_ALU_OPS_PER_CELL),
-            ("pair_kernel (packed intra-task)", stats["cells"] - stats["inter_cells"], t["pair_ms"],
-             PACKED_ALU_OPS_PER_CELL)):
+            (pair_name, stats["cells"] - stats["inter_cells"], t["pair_ms"],
+             TWO_QUERY_ALU_OPS_PER_CELL if two_q_long else PACKED_ALU_OPS_PER_CELL)):
         kms = statistics.mean(kms_list) if kms_list else float("nan")
         ach = ops * kcells / (kms / 1e3) / 1e12 if kcells else 0.0
         per_kernel[name] = {"ms": round(kms, 3), "cells": int(kcells), "achieved": round(ach, 3),
@@ -487,14 +495,14 @@ def roofline(t, peak, peak_source, rate_mhz, traffic):
     return {"bound": "alu", "achieved": dom["achieved"], "peak": round(peak, 3),
             "unit": "Tops/s", "frac": dom["frac"],
             "traffic": traffic(("inter2q_kernel" if two_q else "inter_kernel") if inter
-                               else "pair_kernel"),
+                               else ("pair2q_kernel" if two_q_long else "pair_kernel")),
             "kernel": dominant, "kernel_ms": dom["ms"], "kernel_cells": dom["cells"],
             "kernels": per_kernel,
             "alu_ops_per_cell": dom["alu_ops_per_cell"],
             "peak_source": peak_source,
             "intpeak_clock_mhz": round(rate_mhz, 1),
             "peak_gcups": round(peak * 1e12 / dom["alu_ops_per_cell"] / 1e9, 1),
-            "pair_kernel_ms": per_kernel["pair_kernel (packed intra-task)"]["ms"],
+            "pair_kernel_ms": per_kernel[pair_name]["ms"],
             "recompute_ms": round(statistics.mean(t["recompute_ms"]), 3)}
 
 
@@ -691,6 +699,8 @@ def run_native(args):
         opts["two_query_rows"] = args.two_query_rows
     if args.two_query_pairs is not None:
         opts["two_query_pairs"] = args.two_query_pairs
+    if args.two_query_long is not None:
+        opts["two_query_long"] = args.two_query_long
     if args.wide_min is not None:
         opts["wide_min_len"] = args.wide_min
     if args.wide_min_subject is not None:

@@ -126,13 +126,18 @@ typedef struct {
                                 model expects it to be faster (default), 2 whenever a search
                                 has at least two queries */
   int32_t two_query_rows;    /* query rows per strip of that kernel: 16, 24 or 32 (default) */
-  int32_t two_query_pairs;   /* stream pairs of that kernel (0: the plan's choice, see
-                                sw_plan_search; otherwise at most n_queries / 2) */
+  int32_t two_query_pairs;   /* stream pairs of the two-query layouts, inter- and intra-task
+                                (0: the plan's choice, per layout; otherwise at most
+                                n_queries / 2) */
   int32_t flag_capacity;     /* entries of the plan's list of saturated pairs (8 bytes each);
                                 0: min(max_queries x subjects, 2^20).  More saturated pairs
                                 than this in one search are still scored exactly, in further
                                 rounds of the int32 kernel after the search (see
                                 sw_stats.overflow_rounds) */
+  int32_t two_query_long;    /* intra-task scoring of the long subjects with two queries per
+                                32-bit word against one subject per warp (no per-cell byte
+                                merge): 0 never, 1 when the plan's cost model expects it to be
+                                faster (default), 2 whenever a search has at least two queries */
 } sw_options;
 
 void sw_options_default(sw_options* opt);
@@ -158,6 +163,9 @@ typedef struct {
   int64_t inter_cells;       /* cells scored by the inter-task kernel */
   int64_t inter2_items;      /* (stream pair, half group) items of the two-query inter-task
                                 kernel; 0 when the one-query kernel scored the short subjects */
+  int64_t pair2_items;       /* (stream pair, group of 12 long subjects) items of the two-query
+                                intra-task kernel; 0 when the subject-pair kernels scored the
+                                long subjects */
 } sw_stats;
 
 /* Creates a search context for up to max_queries queries holding up to
@@ -177,22 +185,25 @@ sw_status sw_plan_create(sw_db* db, int32_t max_queries, int64_t max_query_resid
 void sw_plan_destroy(sw_plan* plan);
 
 /* Exact scores of every query against every subject (Eq. 1-3), the batched
- * path: five persistent launches, each taking its work longest first from
- * its own atomic counter -- the packed intra-task kernel over (pair of
- * subjects longer than opt.long_cutoff, query) items, at 32 and at 16 query
- * rows per lane, the two launches side by side on two streams (opt.
- * wide_min_len and opt.wide_min_subject split the items between them); then
- * one of the two packed inter-task kernels for the other subjects: two
- * queries per 32-bit word against one subject per lane, over (pair of query
+ * path: six persistent launches, each taking its work longest first from its
+ * own atomic counter.  First, for the subjects longer than opt.long_cutoff,
+ * one of two packed intra-task layouts: two queries per 32-bit word against
+ * one subject per warp, over (pair of query streams, group of 12 subjects)
+ * items; or two subjects per word, over (pair of subjects, query) items, at
+ * 32 and at 16 query rows per lane, two launches side by side on two streams
+ * (opt.wide_min_len and opt.wide_min_subject split the items between them).
+ * Then one of two packed inter-task layouts for the other subjects: two
+ * queries per word against one subject per lane, over (pair of query
  * streams, half of a group of 64 subjects) items, or two subjects per word,
- * over (query, group of 64 subjects) items (opt.two_query and a cost model
- * choose per search; a single query always takes the latter; the other
- * kernel finds no items); and last the int32 intra-task kernel, which
- * recomputes every pair whose 16-bit score may have saturated (one block per
- * pair; more saturated pairs than opt.flag_capacity are recomputed in further
- * rounds before the call returns).  With gap penalties too large for 16 bits,
- * or opt.force_int32, every pair goes to the int32 kernel instead (one warp
- * per pair).  The packed kernels are compiled with the gap penalties as
+ * over (query, group of 64 subjects) items.  opt.two_query_long and
+ * opt.two_query with a cost model choose each layout per search; a single
+ * query always takes the two-subject ones; the kernels of the other layout
+ * find no items.  Last the int32 intra-task kernel recomputes every pair
+ * whose 16-bit score may have saturated (one block per pair; more saturated
+ * pairs than opt.flag_capacity are recomputed in further rounds before the
+ * call returns).  With gap penalties too large for 16 bits, or
+ * opt.force_int32, every pair goes to the int32 kernel instead (one warp per
+ * pair).  The packed kernels are compiled with the gap penalties as
  * constants for (10, 2) and (11, 1), and read them at run time otherwise.
  * The launch sequence is replayed from a CUDA graph (one per such gap
  * setting) when opt.use_graph is set.

@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libswgb.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["api.cu", "inter_kernel.cu", "inter2q_kernel.cu", "pair_kernel.cu", "intra_kernel.cu", "plain_kernel.cu",
+SOURCES = ["api.cu", "inter_kernel.cu", "inter2q_kernel.cu", "pair_kernel.cu", "pair2q_kernel.cu",
+           "intra_kernel.cu", "plain_kernel.cu",
            "align_kernel.cu", "intpeak.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

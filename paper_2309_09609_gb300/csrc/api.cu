@@ -122,6 +122,7 @@ extern "C" void sw_options_default(sw_options* opt) {
   opt->two_query_rows = 32;
   opt->two_query_pairs = 0;
   opt->flag_capacity = 0;
+  opt->two_query_long = 1;
 }
 
 // ---- small helpers ----------------------------------------------------------------
@@ -429,6 +430,7 @@ struct sw_plan {
   int32_t g_first = 0;      // first inter-task group under the cutoff
   int32_t pair_blocks16 = 0;  // grid of pair_kernel<16>
   int32_t pair_blocks32 = 0;  // grid of pair_kernel<32>
+  int32_t pair2_blocks = 0;   // grid of pair2q_kernel
   // device buffers
   uint8_t* qres = nullptr;
   int64_t* qoff = nullptr;
@@ -540,6 +542,8 @@ extern "C" sw_status sw_plan_create(sw_db* db, int32_t max_queries, int64_t max_
   if (o.two_query_rows != 16 && o.two_query_rows != 24 && o.two_query_rows != 32)
     return sw_set_error(SW_EINVAL, "two_query_rows must be 16, 24 or 32");
   if (o.two_query_pairs < 0) return sw_set_error(SW_EINVAL, "two_query_pairs < 0");
+  if (o.two_query_long < 0 || o.two_query_long > 2)
+    return sw_set_error(SW_EINVAL, "two_query_long must be 0, 1 or 2");
   CUDA_TRY(cudaSetDevice(db->device));
 
   sw_plan* p = new sw_plan();
@@ -608,8 +612,16 @@ extern "C" sw_status sw_plan_create(sw_db* db, int32_t max_queries, int64_t max_
   }
   p->pair_blocks16 = dev_sms * pbps16;
   p->pair_blocks32 = dev_sms * pbps32;
-  // the two widths may run at the same time, each on its own scratch rows
-  const int64_t WP = (int64_t)(p->pair_blocks16 + p->pair_blocks32) * PAIR_WARPS;
+  const int p2bps = pair2q_blocks_per_sm();
+  if (p2bps < 1) {
+    plan_free(p);
+    return sw_set_error(SW_ECUDA, "two-query packed intra-task kernel cannot launch");
+  }
+  p->pair2_blocks = dev_sms * p2bps;
+  // the two widths may run at the same time, each on its own scratch rows;
+  // the two-query kernel runs instead of them and uses the first rows
+  const int64_t WP = std::max<int64_t>((int64_t)(p->pair_blocks16 + p->pair_blocks32) * PAIR_WARPS,
+                                       (int64_t)p->pair2_blocks * pair2q_warps());
   p->scr.pair_rows16 = (int64_t)p->pair_blocks16 * PAIR_WARPS;
 
   cudaError_t e = injected_fault("alloc") ? cudaErrorMemoryAllocation : cudaSuccess;
@@ -626,10 +638,12 @@ extern "C" sw_status sw_plan_create(sw_db* db, int32_t max_queries, int64_t max_
   if (e == cudaSuccess) e = dalloc(&p->qoff, max_queries);
   if (e == cudaSuccess) e = dalloc(&p->qlen, max_queries);
   if (e == cudaSuccess) e = dalloc(&p->qorder, 2 * (size_t)max_queries);  // qorder, then qpair
-  // strips: every query padded to 16-row strips (at least one), and as many
-  // empty halves at most; stream pairs: one per two queries at most
+  // strips of the two tables (the inter-task kernel's, at least 16 rows per
+  // strip, and the intra-task kernel's, 32): every query padded to whole
+  // strips (at least one), and as many empty halves at most; stream pairs:
+  // one per two queries at most, per table
   p->strip_capacity = 2 * (max_query_residues / 16 + 2 * (int64_t)max_queries) + 16;
-  p->spair_capacity = max_queries / 2 + 1;
+  p->spair_capacity = 2 * (max_queries / 2 + 1);
   if (e == cudaSuccess) e = dalloc(&p->strips, (size_t)p->strip_capacity);
   if (e == cudaSuccess) e = dalloc(&p->spairs, (size_t)p->spair_capacity);
   if (e == cudaSuccess) e = dalloc(&p->params, 1);
@@ -691,6 +705,9 @@ static cudaError_t enqueue_kernels(sw_plan* p, cudaStream_t s, bool capturing) {
   if (e == cudaSuccess) e = cudaStreamWaitEvent(p->side, p->fork, 0);
   const int gc = p->gclass;
   if (e == cudaSuccess) e = launch_pairs(32, gc, p->pair_blocks32, p->db->view, p->params, p->state, p->scr, p->side);
+  // the two-query intra-task kernel, when the plan chose it for this search
+  // (the subject-pair kernels then find no items and return at once)
+  if (e == cudaSuccess) e = launch_pair2q(gc, p->pair2_blocks, p->db->view, p->params, p->state, p->scr, p->side);
   if (e == cudaSuccess) e = launch_pairs(16, gc, p->pair_blocks16, p->db->view, p->params, p->state, p->scr, s);
   if (p->opt.overlap_kernels) {
     // the inter-task kernel too, on a third stream and issued after the pair
@@ -744,34 +761,83 @@ static cudaError_t run_kernels(sw_plan* p, cudaStream_t s) {
   return cudaGraphLaunch(graph, s);
 }
 
-// Two queries per word (inter2q_kernel.cu): deals the batch's queries to
-// 2K query streams, longest first, each to the stream with the fewest strips
-// so far (each query padded to whole strips of T rows, at least one), and
-// pairs streams 2k and 2k + 1.  Writes the strip table and the stream pairs
-// to the plan's pinned staging buffers.  Returns K, or 0 when the one-query
-// kernel should score the short subjects instead:
-//   * K (unless the option fixes it) is the smallest power of two, at most
-//     nq / 2, for which the largest item -- the longest group against the
-//     longest stream pair -- is at most 0.35 of one warp's share of the
-//     search: fewer, longer streams pad less (a stream pair is as long as
-//     its longer stream), but an item longer than a warp's share finishes
-//     late; items run longest group first, so the last ones are short;
-//   * with option two_query = 1 the two-query layout must cost less than the
-//     one-query kernel's 32-row strips, counting a two-query word at 0.9 of a
-//     one-query word: measured 0.88 on the paper-shaped search (20 queries)
-//     and 0.93 on a search of two queries (375 and 455 residues), where the
-//     one-query kernel is then the faster.
-static int32_t plan_streams(sw_plan* p, const HostBatch& hb, int32_t nq, int32_t g_first,
-                            int64_t* n_strips) {
-  const int T = p->kc2.variant;
-  const double warps = (double)p->kc2.blocks * p->kc2.warps;
-  const DbView& v = p->db->view;
-  double glen_sum = 0;
-  for (int32_t g = g_first; g < v.groups; g++) glen_sum += p->db->glen_h[g];
-  const double glen_max = g_first < v.groups ? p->db->glen_h[g_first] : 0.0;
+// Splits the queries of one stream pair between its two streams so that the
+// longer stream is as short as the strip counts allow: an exact subset sum
+// over the pair's queries (reachable sums as bit sets, one per prefix of the
+// queries, then a walk back from the largest sum not above half the total).
+// Dealing longest first leaves the two streams of a pair up to a query's
+// length apart; this closes the gap.  Pairs of more than 64 queries keep the
+// dealt split (with many short queries it is already even).
+static void balance_pair(std::vector<int32_t>& a, std::vector<int32_t>& b, int64_t& la,
+                         int64_t& lb, const std::vector<int64_t>& strips_of) {
+  std::vector<int32_t> all(a);
+  all.insert(all.end(), b.begin(), b.end());
+  const size_t n = all.size();
+  const int64_t S = la + lb, H = S / 2;
+  if (n < 2 || n > 64 || std::max(la, lb) == S - H) return;
+  const size_t W = (size_t)(H / 64 + 1);
+  const uint64_t top_mask = (H % 64 == 63) ? ~0ull : ((2ull << (H % 64)) - 1);
+  std::vector<uint64_t> reach((n + 1) * W, 0);
+  reach[0] = 1;  // the empty set sums to 0
+  for (size_t i = 0; i < n; i++) {
+    const uint64_t* src = &reach[i * W];
+    uint64_t* dst = &reach[(i + 1) * W];
+    const int64_t sh = strips_of[all[i]];
+    const size_t ws = (size_t)(sh / 64);
+    const int bs = (int)(sh % 64);
+    for (size_t w = 0; w < W; w++) {
+      uint64_t v = src[w];
+      if (w >= ws) {
+        v |= src[w - ws] << bs;
+        if (bs && w > ws) v |= src[w - ws - 1] >> (64 - bs);
+      }
+      dst[w] = v;
+    }
+    dst[W - 1] &= top_mask;  // sums above H are not kept
+  }
+  const uint64_t* fin = &reach[n * W];
+  int64_t t = H;
+  while (t > 0 && !((fin[t / 64] >> (t % 64)) & 1)) t--;
+  if (S - t >= std::max(la, lb)) return;
+  std::vector<int32_t> taken, rest;
+  int64_t r = t;
+  for (size_t i = n; i-- > 0;) {
+    const uint64_t* prev = &reach[i * W];
+    if ((prev[r / 64] >> (r % 64)) & 1) {
+      rest.push_back(all[i]);  // the sum r is reachable without query i
+    } else {
+      taken.push_back(all[i]);
+      r -= strips_of[all[i]];
+    }
+  }
+  a.assign(rest.rbegin(), rest.rend());
+  b.assign(taken.rbegin(), taken.rend());
+  la = S - t;
+  lb = t;
+}
+
+// Query streams for two queries per word (inter2q_kernel.cu and
+// pair2q_kernel.cu): deals the batch's queries to 2K streams, longest first,
+// each to the stream with the fewest strips so far (each query padded to
+// whole strips of T rows, at least one), pairs streams 2k and 2k + 1 and
+// balances each pair's two streams (balance_pair).
+// Unless fixed_K > 0, K is the smallest power of two, at most nq / 2, for
+// which the largest work item -- the longest column set (len_max) against
+// the longest stream pair -- is at most 0.35 of one worker's share of the
+// search (len_sum columns against every stream pair, over `workers`): fewer,
+// longer streams pad less (a stream pair is as long as its longer stream),
+// but an item longer than a worker's share finishes late; items run longest
+// first, so the last ones are short.  Writes the strip table (per strip: the
+// query of each half, its first row | end bit 31; query -1 for an empty
+// half) to tab and per stream pair (first strip, counted from first_strip,
+// strips) to pairs.  Returns K, or 0 when the table would exceed cap strips;
+// *n_strips is the table's length.
+static int32_t deal_streams(const HostBatch& hb, int32_t nq, int T, int32_t fixed_K,
+                            double workers, double len_max, double len_sum, int4* tab,
+                            int2* pairs, int64_t first_strip, int64_t cap, int64_t* n_strips) {
+  *n_strips = 0;
   std::vector<int64_t> strips_of((size_t)nq);
   for (int32_t i = 0; i < nq; i++) strips_of[i] = std::max<int64_t>(1, (hb.len[i] + T - 1) / T);
-  // longest first (hb.order), each to the stream with the fewest strips
   std::vector<std::vector<int32_t>> streams;
   std::vector<int64_t> load;
   auto deal = [&](int32_t K) {
@@ -785,35 +851,31 @@ static int32_t plan_streams(sw_plan* p, const HostBatch& hb, int32_t nq, int32_t
       streams[best].push_back(q);
       load[best] += strips_of[q];
     }
+    for (int32_t k = 0; k < K; k++)
+      balance_pair(streams[2 * k], streams[2 * k + 1], load[2 * k], load[2 * k + 1], strips_of);
   };
   auto pair_strips = [&](int32_t k) { return std::max(load[2 * k], load[2 * k + 1]); };
-  int32_t K = p->opt.two_query_pairs > 0 ? std::min(p->opt.two_query_pairs, nq / 2) : 1;
+  int32_t K = fixed_K > 0 ? std::min(fixed_K, nq / 2) : 1;
   deal(K);
-  while (p->opt.two_query_pairs == 0 && 2 * K <= nq / 2) {
+  while (fixed_K == 0 && 2 * K <= nq / 2) {
     int64_t smax = 0, ssum = 0;
     for (int32_t k = 0; k < K; k++) {
       smax = std::max(smax, pair_strips(k));
       ssum += pair_strips(k);
     }
-    // largest item vs a warp's share, both in (columns x strips) units
-    if (glen_max * (double)smax <= 0.35 * glen_sum * (double)ssum / warps) break;
+    if (len_max * (double)smax <= 0.35 * len_sum * (double)ssum / workers) break;
     K *= 2;
     deal(K);
   }
-  int64_t total = 0, cost2 = 0, cost1 = 0;
+  int64_t total = 0;
   for (int32_t k = 0; k < K; k++) total += pair_strips(k);
-  if (total > p->strip_capacity) return 0;
-  cost2 = total * T;  // words per column and half-group: S_k strips x T rows
-  for (int32_t i = 0; i < nq; i++) cost1 += (hb.len[i] + 31) / 32 * 32;  // rows per column and group
-  // per column of a 64-subject group: one-query = cost1 words; two-query =
-  // 2 halves x cost2 words at 0.85 each
-  if (p->opt.two_query == 1 && 2.0 * 0.9 * (double)cost2 >= (double)cost1) return 0;
+  if (total > cap) return 0;
   int64_t at = 0;
   for (int32_t k = 0; k < K; k++) {
-    const int64_t S = std::max(load[2 * k], load[2 * k + 1]);
-    p->spairs_h[k] = make_int2((int32_t)at, (int32_t)S);
+    const int64_t S = pair_strips(k);
+    pairs[k] = make_int2((int32_t)(first_strip + at), (int32_t)S);
     // each half walks its stream: query index, first row, end bit
-    int4* tab = p->strips_h + at;
+    int4* t4 = tab + at;
     for (int half = 0; half < 2; half++) {
       const std::vector<int32_t>& st = streams[2 * k + half];
       size_t qi = 0;
@@ -831,11 +893,11 @@ static int32_t plan_streams(sw_plan* p, const HostBatch& hb, int32_t nq, int32_t
           }
         }
         if (half == 0) {
-          tab[s].x = q;
-          tab[s].y = first;
+          t4[s].x = q;
+          t4[s].y = first;
         } else {
-          tab[s].z = q;
-          tab[s].w = first;
+          t4[s].z = q;
+          t4[s].w = first;
         }
       }
     }
@@ -843,6 +905,67 @@ static int32_t plan_streams(sw_plan* p, const HostBatch& hb, int32_t nq, int32_t
   }
   *n_strips = at;
   return K;
+}
+
+// The short subjects' two-query layout (inter2q_kernel.cu): items are
+// (stream pair, half of a 64-subject group), the workers its warps.  Returns
+// K, or 0 when the one-query kernel should score the short subjects instead:
+// with option two_query = 1 the two-query layout must cost less than the
+// one-query kernel's 32-row strips, counting a two-query word at 0.9 of a
+// one-query word (measured 0.88 on the paper-shaped search, 20 queries, and
+// 0.93 on a search of two queries of 375 and 455 residues, where the
+// one-query kernel is then the faster).
+static int32_t plan_streams(sw_plan* p, const HostBatch& hb, int32_t nq, int32_t g_first,
+                            int64_t* n_strips) {
+  const int T = p->kc2.variant;
+  const DbView& v = p->db->view;
+  double glen_sum = 0;
+  for (int32_t g = g_first; g < v.groups; g++) glen_sum += p->db->glen_h[g];
+  const double glen_max = g_first < v.groups ? p->db->glen_h[g_first] : 0.0;
+  const int32_t K = deal_streams(hb, nq, T, p->opt.two_query_pairs,
+                                 (double)p->kc2.blocks * p->kc2.warps, glen_max, glen_sum,
+                                 p->strips_h, p->spairs_h, 0, p->strip_capacity, n_strips);
+  if (K == 0) return 0;
+  const int64_t cost2 = *n_strips * T;  // words per column and half-group: strips x T rows
+  int64_t cost1 = 0;                    // rows per column and group
+  for (int32_t i = 0; i < nq; i++) cost1 += (hb.len[i] + 31) / 32 * 32;
+  if (p->opt.two_query == 1 && 2.0 * 0.9 * (double)cost2 >= (double)cost1) return 0;
+  return K;
+}
+
+// The long subjects' two-query layout (pair2q_kernel.cu), its table placed
+// after the short subjects' (first_strip, first_pair): items are (stream
+// pair, group of PAIR2_GROUP long subjects), the workers its blocks.  Returns
+// K, or 0 when the subject-pair kernels (pair_kernel.cu) should score the
+// long subjects instead: with option two_query_long = 1 when the two-query
+// layout, whose passes are 1024 rows of each stream, costs more than those
+// kernels' passes of 512 or 1024 rows of each query against half as many
+// subject columns, counting a two-query word at 0.85 of a subject-pair word
+// of pair_kernel<32> and a word of pair_kernel<16> at 1.15.
+static int32_t plan_streams_long(sw_plan* p, const HostBatch& hb, int32_t nq, int64_t n_long,
+                                 int64_t first_strip, int32_t first_pair, int64_t* n_strips) {
+  *n_strips = 0;
+  if (nq < 2 || n_long <= 0) return 0;
+  const int32_t* clen = p->db->clen_h.data();
+  double len_sum = 0;
+  for (int64_t s = 0; s < n_long; s += PAIR2_GROUP) len_sum += clen[s];
+  const int32_t K = deal_streams(hb, nq, PAIR2_STRIP, p->opt.two_query_pairs,
+                                 (double)p->pair2_blocks, clen[0],
+                                 len_sum, p->strips_h + first_strip, p->spairs_h + first_pair,
+                                 first_strip, p->strip_capacity - first_strip, n_strips);
+  if (K == 0 || p->opt.two_query_long == 2) return K;
+  // words per column of a subject
+  double two = 0, one = 0;
+  for (int32_t k = 0; k < K; k++) {
+    const int64_t S = p->spairs_h[first_pair + k].y;
+    two += (double)((S + 31) / 32) * 32 * PAIR2_STRIP;
+  }
+  for (int32_t i = 0; i < nq; i++) {
+    const int64_t m = hb.len[i];
+    one += pair_wide((int32_t)m) ? (double)((m + 1023) / 1024 * 1024) / 2
+                                 : 1.15 * (double)((m + 511) / 512 * 512) / 2;
+  }
+  return 0.85 * two < one ? K : 0;
 }
 
 // Stages a batch into the plan and enqueues everything up to (not including)
@@ -926,6 +1049,28 @@ static sw_status plan_enqueue(sw_plan* p, const HostBatch& hb, int32_t nq, int32
       P.n_spairs = K;
       P.n_inter2_items = (int64_t)K * 2 * (v.groups - gf);
       P.n_inter_items = 0;
+    } else {
+      n_strips = 0;
+    }
+  }
+  // and for the long subjects (the subject-pair kernels then have no items);
+  // its table follows the short subjects' in the same buffers
+  P.strips2 = p->strips;
+  P.spairs2 = p->spairs + P.n_spairs;
+  P.n_spairs2 = 0;
+  P.n_pair2_items = 0;
+  int64_t n_strips2 = 0;
+  if (packed && n_long > 0 && nq >= 2 && p->opt.two_query_long > 0) {
+    const int32_t K2 = plan_streams_long(p, hb, nq, n_long, n_strips, P.n_spairs, &n_strips2);
+    if (K2 > 0) {
+      P.n_spairs2 = K2;
+      P.n_pair2_items = (int64_t)K2 * ((n_long + PAIR2_GROUP - 1) / PAIR2_GROUP);
+      P.pair_queries = 0;
+      P.n_wide_pairs = 0;
+      P.nq_pair32 = 0;
+      P.nq_pair16 = 0;
+    } else {
+      n_strips2 = 0;
     }
   }
   memcpy(p->qoff_h, hb.off.data(), sizeof(int64_t) * nq);
@@ -940,9 +1085,11 @@ static sw_status plan_enqueue(sw_plan* p, const HostBatch& hb, int32_t nq, int32
     CUDA_TRY(cudaMemcpyAsync(p->qlen, p->qlen_h, sizeof(int32_t) * nq, cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(p->qorder, p->qorder_h, sizeof(int32_t) * 2 * nq, cudaMemcpyHostToDevice, s));
   }
-  if (P.n_spairs > 0) {
-    CUDA_TRY(cudaMemcpyAsync(p->strips, p->strips_h, sizeof(int4) * n_strips, cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemcpyAsync(p->spairs, p->spairs_h, sizeof(int2) * P.n_spairs, cudaMemcpyHostToDevice, s));
+  if (P.n_spairs + P.n_spairs2 > 0) {
+    CUDA_TRY(cudaMemcpyAsync(p->strips, p->strips_h, sizeof(int4) * (n_strips + n_strips2),
+                             cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(p->spairs, p->spairs_h, sizeof(int2) * (P.n_spairs + P.n_spairs2),
+                             cudaMemcpyHostToDevice, s));
   }
   CUDA_TRY(cudaMemcpyAsync(p->params, p->params_h, sizeof(SearchParams), cudaMemcpyHostToDevice, s));
   p->stream = s;
@@ -954,9 +1101,10 @@ static sw_status plan_enqueue(sw_plan* p, const HostBatch& hb, int32_t nq, int32
   p->pending.cells = qsum * p->db->residues;
   p->pending.inter_items = P.n_inter_items;
   p->pending.inter2_items = P.n_inter2_items;
+  p->pending.pair2_items = P.n_pair2_items;
   p->pending.intra_items = n_long * nq;  // (query, long subject) pairs, packed or int32
   p->pending.inter_cells = qsum * (p->db->residues - p->db->cres_h[n_long]);
-  p->pending.kernels_launched = 5;
+  p->pending.kernels_launched = 6;
   return SW_OK;
 }
 

@@ -68,10 +68,16 @@ struct SearchParams {
   const int4* strips;
   const int2* spairs;
   int64_t n_inter2_items; // stream pairs x 2 x inter groups (0: the one-query kernel runs)
+  // two queries per word for the long subjects (pair2q_kernel.cu): a strip
+  // table of 32-row strips and its stream pairs, in the same format
+  const int4* strips2;
+  const int2* spairs2;
+  int64_t n_pair2_items;  // stream pairs x groups of PAIR2_GROUP long subjects (0: pair_kernel runs)
   int64_t n_intra_items;  // n_long x nq  (int32 intra-task items, when the packed path is off)
   int64_t n_inter_items;  // inter groups x nq  (packed inter-task items)
   int32_t nq;
   int32_t n_spairs;       // stream pairs of the two-query kernel
+  int32_t n_spairs2;      // stream pairs of the two-query intra-task kernel
   int32_t pair_queries;   // nq when the packed path scores the long subjects, else 0
   int32_t n_wide_pairs;   // subject pairs [0, n_wide_pairs) may go to pair_kernel<32> ...
   int32_t nq_pair32;      // ... with these queries (qpair[0, nq_pair32)); the narrow
@@ -94,6 +100,7 @@ struct SearchState {
   unsigned long long pair_work32; // next work item (pair_kernel<32>)
   unsigned long long intra_work;  // next int32 intra-task item (per warp)
   unsigned long long work2;       // next work item (two-query inter-task kernel)
+  unsigned long long pair2_work;  // next work item (two-query intra-task kernel, per block)
   unsigned int status;            // reserved: error bits raised on the device
   unsigned int pad;
 };
@@ -175,6 +182,16 @@ size_t pair_smem_bytes(int rows);
 cudaError_t launch_pairs(int rows, int gclass, int blocks, const DbView& db,
                          const SearchParams* params, SearchState* state, const Scratch& scr,
                          cudaStream_t stream);
+// Packed intra-task kernel with two queries per word, long subjects
+// (pair2q_kernel.cu): one block of pair2q_warps() warps per SM, one subject
+// per warp, 32-row strips; scratch: the pair_border rows [0, blocks x warps).
+constexpr int PAIR2_STRIP = 32;  // rows per strip of its strip table
+constexpr int PAIR2_GROUP = 12;  // subjects per item (the warps of a block)
+int pair2q_warps();
+size_t pair2q_smem_bytes();
+int pair2q_blocks_per_sm();
+cudaError_t launch_pair2q(int gclass, int blocks, const DbView& db, const SearchParams* params,
+                          SearchState* state, const Scratch& scr, cudaStream_t stream);
 // pair_kernel<32> costs about 0.85 of pair_kernel<16> per cell it computes
 // but pads a query to 1024-row passes instead of 512: a query of m residues
 // goes to the wide kernel when 0.85 * ceil(m / 1024) * 1024 is below

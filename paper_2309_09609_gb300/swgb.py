@@ -41,7 +41,7 @@ class Options(ctypes.Structure):
                 ("wide_min_subject", ctypes.c_int32), ("inter_columns", ctypes.c_int32),
                 ("overlap_kernels", ctypes.c_int32), ("two_query", ctypes.c_int32),
                 ("two_query_rows", ctypes.c_int32), ("two_query_pairs", ctypes.c_int32),
-                ("flag_capacity", ctypes.c_int32)]
+                ("flag_capacity", ctypes.c_int32), ("two_query_long", ctypes.c_int32)]
 
 
 class Alignment(ctypes.Structure):
@@ -56,7 +56,8 @@ class Stats(ctypes.Structure):
                 ("overflow_rounds", ctypes.c_int32), ("kernels_launched", ctypes.c_int32),
                 ("search_ms", ctypes.c_float), ("recompute_ms", ctypes.c_float),
                 ("pair_ms", ctypes.c_float), ("pad_", ctypes.c_int32),
-                ("inter_cells", ctypes.c_int64), ("inter2_items", ctypes.c_int64)]
+                ("inter_cells", ctypes.c_int64), ("inter2_items", ctypes.c_int64),
+                ("pair2_items", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -68,7 +68,8 @@ def test_options_struct_layout_matches_the_header(lib):
         "rows_per_thread": 32, "warps_per_block": 8, "long_cutoff": 1500, "intra_rows": 8,
         "use_graph": 1, "force_int32": 0, "auto_cutoff": 0, "wide_min_len": 0,
         "wide_min_subject": 4096, "inter_columns": 8, "overlap_kernels": 0, "two_query": 1,
-        "two_query_rows": 32, "two_query_pairs": 0, "flag_capacity": 0}
+        "two_query_rows": 32, "two_query_pairs": 0, "flag_capacity": 0,
+        "two_query_long": 1}
     header = open(os.path.join(ROOT, "include", "swgb.h")).read()
     body = re.search(r"typedef struct \{([^{}]*)\} sw_options;", header).group(1)
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)

@@ -25,7 +25,8 @@ def built():
 def all_paths(q, db, go=10, ge=2, matrix=None, plain=True, **opts):
     """Scores through every path: the one-shot search, a plan (twice: the
     second replays its graph) with `opts`, the same plan forced to the
-    one-query and to the two-query inter-task kernel, and the plain
+    one-query and to the two-query inter-task kernel and to the
+    subject-pair and the two-query intra-task kernel, and the plain
     baseline.  Returns them with the stats of the `opts` plan."""
     d = swgb.Database.from_seqset(db)
     res = {"search": d.search(q.res, q.lens, go, ge, matrix)}
@@ -39,6 +40,14 @@ def all_paths(q, db, go=10, ge=2, matrix=None, plain=True, **opts):
             res[f"plan_two_query_{tq}"] = pk.search(q.res, q.lens, go, ge, matrix)
             if tq == 2 and len(q) >= 2 and st["inter_cells"] > 0 and not opts.get("force_int32"):
                 assert pk.stats()["inter2_items"] > 0 and pk.stats()["inter_items"] == 0
+    if "two_query_long" not in opts:
+        for tq in (0, 2):
+            pk = d.plan(max(len(q), 1), max(q.total, 1), two_query_long=tq, **opts)
+            res[f"plan_two_query_long_{tq}"] = pk.search(q.res, q.lens, go, ge, matrix)
+            if tq == 0:
+                assert pk.stats()["pair2_items"] == 0
+            elif len(q) >= 2 and st["inter_cells"] > 0 and st["intra_items"] > 0:
+                assert pk.stats()["pair2_items"] > 0
     if plain:
         res["plain"] = d.search_plain(q.res, q.lens, go, ge, matrix)
     return res, st
@@ -108,6 +117,87 @@ def test_two_query_saturation_in_one_half(rows):
     assert_exact({"2q": got}, want)
 
 
+@pytest.mark.parametrize("gaps", [(10, 2), (11, 1), (6, 3)])   # the two gap classes, general
+def test_two_query_long_streams_ragged(gaps):
+    # Long subjects scored two queries per word, one subject per warp:
+    # thirteen queries around the 32-row strips and 1024-row passes (and of
+    # length 0 and 1) in query streams, subjects around the 128-column residue
+    # blocks; stream pairs chosen by the plan (here one query per stream) and
+    # forced to one (queries changing inside a half, inside a pass).
+    rng = np.random.default_rng(80 + gaps[1])
+    q = seqset(rng, [0, 1, 31, 32, 33, 100, 1023, 1024, 1025, 2100, 57, 400, 7])
+    lens = [101, 127, 128, 129, 255, 256, 257, 383, 384, 385, 1000, 2500]
+    db = concat(seqset(rng, lens + list(rng.integers(150, 1200, 35))),
+                seqset(rng, rng.integers(0, 100, 150)))
+    want = oracle_all(q, db, *gaps)
+    d = swgb.Database.from_seqset(db)
+    for idx in (list(range(13)), [7, 9], [0, 1, 2], [9, 0, 5, 12, 6]):
+        sub = q.subset(idx)
+        groups = None                        # items of one stream pair: the subject groups
+        for pairs in (1, 0):
+            p = d.plan(len(sub), max(sub.total, 1), two_query_long=2, two_query_pairs=pairs,
+                       long_cutoff=100)
+            got = p.search(sub.res, sub.lens, *gaps)
+            items = p.stats()["pair2_items"]
+            groups = groups or items
+            assert items > 0 and items % groups == 0
+            assert_exact({f"{idx} pairs={pairs}": got}, want[idx])
+
+
+def test_two_query_long_query_boundaries_at_pass_edges():
+    # Forced to one stream pair, the streams are dealt longest first to the
+    # shorter stream, so these batches put query boundaries at the edges of a
+    # 1024-row pass: [2112, 1024, 1024] starts the third query at lane 0 of
+    # the second pass in half 1 (half 0: one query of 66 strips, empty
+    # strips after it); [1056, 992, 64] gives half 1 31 strips, then a query
+    # of 2 strips across lane 31 of the first pass and lane 0 of the second;
+    # [1000, 40 x 9] puts nine queries in half 1, several in one pass.
+    rng = np.random.default_rng(90)
+    db = concat(seqset(rng, list(rng.integers(130, 900, 20)) + [0, 0, 1, 128]),
+                seqset(rng, rng.integers(1, 60, 20)))
+    for lens in ([2112, 1024, 1024], [1056, 992, 64], [1000] + [40] * 9):
+        q = seqset(rng, lens)
+        want = oracle_all(q, db)
+        d = swgb.Database.from_seqset(db)
+        p = d.plan(len(q), q.total, two_query_long=2, two_query_pairs=1, long_cutoff=100)
+        got = p.search(q.res, q.lens)
+        assert p.stats()["pair2_items"] > 0
+        assert_exact({str(lens): got}, want)
+
+
+def test_two_query_long_small_group_and_empty_subjects():
+    # every subject in one 64-subject group whose longest exceeds the
+    # cutoff: the long part is all 13 subjects -- one item of 12 subjects and
+    # one of a single subject (the other warps idle), two of length 0
+    rng = np.random.default_rng(91)
+    db = seqset(rng, [700, 300, 129, 0, 0, 5, 64, 1, 2, 900, 33, 17, 128])
+    q = seqset(rng, [1, 40, 300, 1100, 77])
+    d = swgb.Database.from_seqset(db)
+    p = d.plan(len(q), q.total, two_query_long=2, long_cutoff=500)
+    got = p.search(q.res, q.lens)
+    assert p.stats()["pair2_items"] >= 2 and p.stats()["inter_cells"] == 0
+    assert_exact({"small": got}, oracle_all(q, db))
+
+
+def test_two_query_long_saturation_in_one_half():
+    # saturating queries beside ordinary ones against long subjects: the
+    # saturated half is flagged and recomputed, the other stays exact; one
+    # stream pair, so a saturating query is followed by others in its half
+    rng = np.random.default_rng(92)
+    w = lambda k: "W" * k
+    q = concat(from_text(w(2990), w(2978) + "A" * 40, "HEAGAWGHEE"), seqset(rng, [30, 500, 2000]))
+    db = concat(from_text(w(2977), w(2978), w(3000) + "K" * 20),
+                seqset(rng, rng.integers(200, 1500, 30)), seqset(rng, rng.integers(1, 90, 50)))
+    want = oracle_all(q, db)
+    assert want.max() > 32767
+    d = swgb.Database.from_seqset(db)
+    for pairs in (0, 1):
+        p = d.plan(len(q), q.total, two_query_long=2, two_query_pairs=pairs, long_cutoff=100)
+        got = p.search(q.res, q.lens)
+        assert p.stats()["recomputed_pairs"] >= 4 and p.stats()["pair2_items"] > 0
+        assert_exact({f"pairs={pairs}": got}, want)
+
+
 def test_full_alphabet_and_asymmetric_matrix():
     rng = np.random.default_rng(3)
     m = rand_matrix(rng, -6, 9, symmetric=False)
@@ -152,7 +242,7 @@ def test_pair_kernel_widths_split_the_queries():
     rng = np.random.default_rng(42)
     db = seqset(rng, list(rng.integers(600, 2500, size=41)) + list(rng.integers(1, 300, size=70)))
     q = seqset(rng, [1, 500, 513, 1000, 1025, 1100, 2049, 3073])
-    res, st = all_paths(q, db, long_cutoff=550, plain=False)
+    res, st = all_paths(q, db, long_cutoff=550, plain=False, two_query_long=0)
     assert st["intra_items"] >= 41 * len(q)
     assert_exact(res, oracle_all(q, db))
 
@@ -165,7 +255,8 @@ def test_pair_kernel_wide_subject_prefix():
     rng = np.random.default_rng(43)
     db = seqset(rng, list(rng.integers(600, 2000, size=700)) + list(rng.integers(1, 300, size=50)))
     q = seqset(rng, [513, 1000, 3073, 500, 1100, 700, 900, 2049])
-    res, st = all_paths(q, db, long_cutoff=550, plain=False, wide_min_subject=1300)
+    res, st = all_paths(q, db, long_cutoff=550, plain=False, wide_min_subject=1300,
+                        two_query_long=0)
     assert st["intra_items"] >= 700 * len(q)
     assert_exact(res, oracle_all(q, db))
 
@@ -273,7 +364,8 @@ def test_flag_list_overflow_is_recomputed_in_rounds():
     assert n_sat > 100
     d = swgb.Database.from_seqset(db)
     for opts in (dict(flag_capacity=7, long_cutoff=300), dict(flag_capacity=7, use_graph=0),
-                 dict(flag_capacity=7, two_query=2), dict(flag_capacity=7, two_query=0)):
+                 dict(flag_capacity=7, two_query=2), dict(flag_capacity=7, two_query=0),
+                 dict(flag_capacity=7, long_cutoff=300, two_query_long=2)):
         p = d.plan(len(q), q.total, **opts)
         for _ in range(2):                                   # a plan reused after an overflow
             got = p.search(q.res, q.lens, 10, 2, m)          # scores to host memory
