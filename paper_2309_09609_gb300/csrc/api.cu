@@ -823,18 +823,20 @@ static void balance_pair(std::vector<int32_t>& a, std::vector<int32_t>& b, int64
 // balances each pair's two streams (balance_pair).
 // Unless fixed_K > 0, K is the smallest power of two, at most nq / 2, for
 // which the largest work item -- the longest column set (len_max) against
-// the longest stream pair -- is at most 0.35 of one worker's share of the
+// the longest stream pair -- is at most `share` of one worker's share of the
 // search (len_sum columns against every stream pair, over `workers`): fewer,
-// longer streams pad less (a stream pair is as long as its longer stream),
-// but an item longer than a worker's share finishes late; items run longest
-// first, so the last ones are short.  Writes the strip table (per strip: the
+// longer streams pad less (a stream pair is as long as its longer stream,
+// and the fewer queries a pair holds the less evenly its two streams
+// split), but an item longer than a worker's share finishes late; items run
+// longest first, so the last ones are short.  Writes the strip table (per strip: the
 // query of each half, its first row | end bit 31; query -1 for an empty
 // half) to tab and per stream pair (first strip, counted from first_strip,
 // strips) to pairs.  Returns K, or 0 when the table would exceed cap strips;
 // *n_strips is the table's length.
 static int32_t deal_streams(const HostBatch& hb, int32_t nq, int T, int32_t fixed_K,
-                            double workers, double len_max, double len_sum, int4* tab,
-                            int2* pairs, int64_t first_strip, int64_t cap, int64_t* n_strips) {
+                            double workers, double share, double len_max, double len_sum,
+                            int4* tab, int2* pairs, int64_t first_strip, int64_t cap,
+                            int64_t* n_strips) {
   *n_strips = 0;
   std::vector<int64_t> strips_of((size_t)nq);
   for (int32_t i = 0; i < nq; i++) strips_of[i] = std::max<int64_t>(1, (hb.len[i] + T - 1) / T);
@@ -863,7 +865,7 @@ static int32_t deal_streams(const HostBatch& hb, int32_t nq, int T, int32_t fixe
       smax = std::max(smax, pair_strips(k));
       ssum += pair_strips(k);
     }
-    if (len_max * (double)smax <= 0.35 * len_sum * (double)ssum / workers) break;
+    if (len_max * (double)smax <= share * len_sum * (double)ssum / workers) break;
     K *= 2;
     deal(K);
   }
@@ -923,7 +925,7 @@ static int32_t plan_streams(sw_plan* p, const HostBatch& hb, int32_t nq, int32_t
   for (int32_t g = g_first; g < v.groups; g++) glen_sum += p->db->glen_h[g];
   const double glen_max = g_first < v.groups ? p->db->glen_h[g_first] : 0.0;
   const int32_t K = deal_streams(hb, nq, T, p->opt.two_query_pairs,
-                                 (double)p->kc2.blocks * p->kc2.warps, glen_max, glen_sum,
+                                 (double)p->kc2.blocks * p->kc2.warps, 0.35, glen_max, glen_sum,
                                  p->strips_h, p->spairs_h, 0, p->strip_capacity, n_strips);
   if (K == 0) return 0;
   const int64_t cost2 = *n_strips * T;  // words per column and half-group: strips x T rows
@@ -935,7 +937,10 @@ static int32_t plan_streams(sw_plan* p, const HostBatch& hb, int32_t nq, int32_t
 
 // The long subjects' two-query layout (pair2q_kernel.cu), its table placed
 // after the short subjects' (first_strip, first_pair): items are (stream
-// pair, group of PAIR2_GROUP long subjects), the workers its blocks.  Returns
+// pair, group of PAIR2_GROUP long subjects), the workers its blocks, and the
+// largest item may be one worker's share (on the paper-shaped search's long
+// subjects, 1, 2, 4 and 8 stream pairs took 45.4, 35.6, 40.0 and 44.2 ms;
+// the rule picks 2 there, and 1 on the long-sequence workload).  Returns
 // K, or 0 when the subject-pair kernels (pair_kernel.cu) should score the
 // long subjects instead: with option two_query_long = 1 when the two-query
 // layout, whose passes are 1024 rows of each stream, costs more than those
@@ -950,7 +955,7 @@ static int32_t plan_streams_long(sw_plan* p, const HostBatch& hb, int32_t nq, in
   double len_sum = 0;
   for (int64_t s = 0; s < n_long; s += PAIR2_GROUP) len_sum += clen[s];
   const int32_t K = deal_streams(hb, nq, PAIR2_STRIP, p->opt.two_query_pairs,
-                                 (double)p->pair2_blocks, clen[0],
+                                 (double)p->pair2_blocks, 1.0, clen[0],
                                  len_sum, p->strips_h + first_strip, p->spairs_h + first_pair,
                                  first_strip, p->strip_capacity - first_strip, n_strips);
   if (K == 0 || p->opt.two_query_long == 2) return K;
