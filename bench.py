@@ -322,8 +322,6 @@ CSRC = os.path.join(ROOT, "paper_2309_09609_gb300", "csrc")
 TRAFFIC_RECORDS = {
     ("inter2q_kernel", "paper-search"): ("inter2q_kernel_paper-search_traffic.txt",
                                          ("inter2q_kernel.cu", "device_common.cuh")),
-    ("pair_kernel", "long"): ("pair_kernel_long-sequences_traffic.txt",
-                              ("pair_kernel.cu", "device_common.cuh")),
     ("pair2q_kernel", "long"): ("pair2q_kernel_long-sequences_traffic.txt",
                                 ("pair2q_kernel.cu", "device_common.cuh")),
 }

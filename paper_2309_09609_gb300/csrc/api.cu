@@ -628,7 +628,8 @@ extern "C" sw_status sw_plan_create(sw_db* db, int32_t max_queries, int64_t max_
   const int64_t nres = std::max<int64_t>(max_query_residues, 1);
   p->scr.inter_stride_vec = (int64_t)(L_inter / CHUNK) * 4 * 32;
   p->scr.intra_stride = std::max(v.max_len, 1);
-  p->scr.pair_stride = std::max(v.max_len, 1);
+  // (+4: the two-query pair kernel loads its border 4 columns ahead)
+  p->scr.pair_stride = std::max(v.max_len, 1) + 4;
   p->scr.flag_capacity = o.flag_capacity > 0
                             ? (int64_t)o.flag_capacity
                             : std::min<int64_t>((int64_t)max_queries * std::max<int64_t>(v.n, 1),

@@ -214,6 +214,9 @@ pair2q_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Sc
           A[q] = lane_off;
         }
         uint32_t hdiag = GO2, out_h = GO2, out_f = 0u;
+        // steady state: lane 0's border of columns t .. t + 3, slot t mod 4
+        uint2 bq[4] = {make_uint2(0u, 0u), make_uint2(0u, 0u), make_uint2(0u, 0u),
+                       make_uint2(0u, 0u)};
         const bool last_pass = (p == npass - 1);
         const int steps = n + 32 * PQ - 1;
         // ring position of column t0 - PQ*lane; a multiple of 4, as is P2_RING
@@ -233,9 +236,18 @@ pair2q_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Sc
           uint32_t in_h = __shfl_up_sync(FULL, out_h, 1);
           uint32_t in_f = __shfl_up_sync(FULL, out_f, 1);
           // lane 0's top border, column t, from the previous pass: every lane
-          // loads the same word (one broadcast, no branch); in the steady state
-          // t < n, so the index needs no clamp
-          const uint2 bv = CHECK ? hb[min(t, n - 1)] : hb[t];
+          // loads the same word (one broadcast, no branch).  In the steady
+          // state it was loaded four steps earlier (its column is rewritten by
+          // lane 31 only 127 steps after lane 0 reads it), and this step loads
+          // column t + 4: t < n there, and the border rows have 4 columns of
+          // slack past the longest subject
+          uint2 bv;
+          if constexpr (CHECK) {
+            bv = hb[min(t, n - 1)];
+          } else {
+            bv = bq[U];
+            bq[U] = hb[t + 4];
+          }
           if (lane == 0) {
             in_h = bv.x;
             in_f = bv.y;
@@ -304,6 +316,10 @@ pair2q_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Sc
         static_assert(32 * PQ == 128, "the ramp must end on a residue block boundary");
         int t0 = 0;
         for (; t0 < 32 * PQ; t0 += 4) block(t0, std::true_type{}, std::true_type{});
+        if (t0 + 128 <= n) {  // the first steady block's first four border words
+#pragma unroll
+          for (int u = 0; u < 4; u++) bq[u] = hb[t0 + u];
+        }
 #pragma unroll 1
         for (; t0 + 128 <= n; t0 += 128) {
           load_block((t0 >> 7) + 1);

@@ -29,13 +29,18 @@ def test_traffic_record_applies_only_to_the_profiled_kernel_and_workload():
     assert bench.profiled_traffic(_args(rows=16)) is None
     assert bench.profiled_traffic(_args(cutoff=3000)) is None
     assert bench.profiled_traffic(_args(workload="long")) is None        # not the inter kernel's
-    assert bench.profiled_traffic(_args(workload="batched-uneven"), "pair_kernel") is None
+    assert bench.profiled_traffic(_args(workload="batched-uneven"), "pair2q_kernel") is None
     assert bench.profiled_traffic(_args(), "inter_kernel") is None      # no record of that kernel
+    assert bench.profiled_traffic(_args(workload="long"), "pair_kernel") is None
     assert bench.profiled_traffic(_args(two_query=0)) is None
-    long = bench.profiled_traffic(_args(workload="long"), "pair_kernel")
-    rec = bench.traffic_record(os.path.join(ROOT, "profiles",
-                                            bench.TRAFFIC_RECORDS[("pair_kernel", "long")][0]))
-    assert long is None or long == int(rec["dram_bytes_per_launch"])
+    assert bench.profiled_traffic(_args(workload="long", two_query_long=0), "pair2q_kernel") is None
+    long = bench.profiled_traffic(_args(workload="long"), "pair2q_kernel")
+    path = os.path.join(ROOT, "profiles", bench.TRAFFIC_RECORDS[("pair2q_kernel", "long")][0])
+    if os.path.exists(path):
+        rec = bench.traffic_record(path)
+        assert long is None or long == int(rec["dram_bytes_per_launch"])
+    else:
+        assert long is None
 
 
 def test_workload_query_subset():
