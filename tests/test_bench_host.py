@@ -77,3 +77,11 @@ def test_paper_arch_efficiency_follows_eq5():
     assert abs(r["peak_gcups"] - 46 * 64 * 1725e6 / 12 / 1e9) < 0.1
     assert abs(r["value"] - 280.2 / (46 * 64 * 1725e6 / 12 / 1e9)) < 1e-4
     assert bench.paper_arch_efficiency(5965.0, 62.5, 152, 2070.0)["value"] > 1   # packed
+
+
+def test_l2_flush_only_when_the_database_fits_in_l2():
+    # two device layouts of about one byte per residue each
+    assert bench.l2_flush_bytes(205_000_000) == 0                 # paper-shaped database
+    assert bench.l2_flush_bytes(36_036_930) == 2 * bench.L2_BYTES  # batched-uneven database
+    assert bench.l2_note(205_000_000).startswith("no flush")
+    assert bench.l2_note(36_036_930).startswith("L2 flushed")
