@@ -79,9 +79,14 @@ __device__ __forceinline__ void q2_wave(uint32_t (&Hp)[T], uint32_t (&E)[T], uin
 #pragma unroll
   for (int c = 0; c < W; c++) {
     const int cc = C0 + c;
-    const uint32_t code = ((cc < 4 ? rr.x : rr.y) >> (8 * (cc & 3))) & 0xffu;
-    cb[c] = code < Q2COMMON ? code * (RB * 128) + p16
-                            : Q2Shape<T>::RARE + (code - Q2COMMON) * 16;
+    const uint32_t code = prmt(cc < 4 ? rr.x : rr.y, 0u, 0x4440u + (cc & 3));  // byte cc % 4
+    // base(code) as the smaller of the two layouts' offsets: a standard code's
+    // (code * RB * 128 + p16, at most RARE - RB * 128 + 112) is below any rare
+    // one's (RARE + (code - 20) * 16, at least RARE - 320), and for a rare code
+    // the replicated formula gives at least RARE + p16; two multiply-adds on
+    // the FMA pipe and one min instead of a compare and select
+    cb[c] = min(imad(code, (uint32_t)(RB * 128), (uint32_t)p16),
+                imad(code, 16u, (uint32_t)(Q2Shape<T>::RARE - Q2COMMON * 16)));
   }
   uint4 pw[W];
   uint32_t htop[W], f[W], last[W], last2[W], bottom[W];
