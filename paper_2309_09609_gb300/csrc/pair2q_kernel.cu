@@ -224,7 +224,9 @@ pair2q_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Sc
         // one step of the wavefront.  CHECK: some quarter may lie outside the
         // columns (ramp and drain); RING: this step may start a 128-column
         // residue block (the steady state refills the ring before each block)
-        auto step = [&](const int t, auto checked, auto slot, auto ringed) {
+        // MASK: some lane's strip starts a query (the steady state of a pass
+        // in which none does leaves the top borders as they come)
+        auto step = [&](const int t, auto checked, auto slot, auto ringed, auto masked) {
           constexpr bool CHECK = decltype(checked)::value;
           constexpr int U = decltype(slot)::value;  // t mod 4
           if constexpr (U == 0 && decltype(ringed)::value) {
@@ -252,8 +254,10 @@ pair2q_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Sc
             in_h = bv.x;
             in_f = bv.y;
           }
-          in_h = (in_h & keep) | gtop;  // H(0, j) = 0 above a query's first row
-          in_f &= keep;                 // F(1, j) = -Go
+          if constexpr (decltype(masked)::value) {
+            in_h = (in_h & keep) | gtop;  // H(0, j) = 0 above a query's first row
+            in_f &= keep;                 // F(1, j) = -Go
+          }
           const int c0 = t - PQ * lane;  // quarter 0's column
           A[U] = lane_off + (uint32_t)ring[pos + U] * P2_CODE_BYTES;
           uint32_t nh[PQ], nf[PQ];
@@ -302,11 +306,11 @@ pair2q_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Sc
             qf1[q] = nf[q];
           }
         };
-        auto block = [&](const int t0, auto checked, auto ringed) {
-          step(t0, checked, std::integral_constant<int, 0>{}, ringed);
-          step(t0 + 1, checked, std::integral_constant<int, 1>{}, ringed);
-          step(t0 + 2, checked, std::integral_constant<int, 2>{}, ringed);
-          step(t0 + 3, checked, std::integral_constant<int, 3>{}, ringed);
+        auto block = [&](const int t0, auto checked, auto ringed, auto masked) {
+          step(t0, checked, std::integral_constant<int, 0>{}, ringed, masked);
+          step(t0 + 1, checked, std::integral_constant<int, 1>{}, ringed, masked);
+          step(t0 + 2, checked, std::integral_constant<int, 2>{}, ringed, masked);
+          step(t0 + 3, checked, std::integral_constant<int, 3>{}, ringed, masked);
           pos = pos + 4 == P2_RING ? 0 : pos + 4;
         };
         // ramp (every lane's quarters enter), steady state in whole 128-column
@@ -315,19 +319,30 @@ pair2q_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Sc
         // block may run past `steps`, where every quarter is outside
         static_assert(32 * PQ == 128, "the ramp must end on a residue block boundary");
         int t0 = 0;
-        for (; t0 < 32 * PQ; t0 += 4) block(t0, std::true_type{}, std::true_type{});
+        for (; t0 < 32 * PQ; t0 += 4)
+          block(t0, std::true_type{}, std::true_type{}, std::true_type{});
         if (t0 + 128 <= n) {  // the first steady block's first four border words
 #pragma unroll
           for (int u = 0; u < 4; u++) bq[u] = hb[t0 + u];
         }
+        // no lane's strip starts a query in most passes of long streams
+        const bool any_start = __any_sync(FULL, keep != 0xffffffffu);
 #pragma unroll 1
         for (; t0 + 128 <= n; t0 += 128) {
           load_block((t0 >> 7) + 1);
           __syncwarp();
+          if (any_start) {
 #pragma unroll 1
-          for (int b = 0; b < 128; b += 4) block(t0 + b, std::false_type{}, std::false_type{});
+            for (int b = 0; b < 128; b += 4)
+              block(t0 + b, std::false_type{}, std::false_type{}, std::true_type{});
+          } else {
+#pragma unroll 1
+            for (int b = 0; b < 128; b += 4)
+              block(t0 + b, std::false_type{}, std::false_type{}, std::false_type{});
+          }
         }
-        for (; t0 < steps; t0 += 4) block(t0, std::true_type{}, std::true_type{});
+        for (; t0 < steps; t0 += 4)
+          block(t0, std::true_type{}, std::true_type{}, std::true_type{});
       }
       // S' of each query over its lanes of this pass (and the previous passes)
       int va = (int)(int16_t)(smax & 0xffffu), vb = (int)(int16_t)(smax >> 16);
