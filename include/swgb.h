@@ -330,6 +330,27 @@ sw_status sw_search_pairs_noalloc(const uint8_t* queries, const int64_t* q_offse
                                   int32_t gap_open, int32_t gap_extend, const int8_t* matrix,
                                   int32_t* scores, void* stream);
 
+/* The query streams of the two-query kernels, for inspection and tests (host
+ * only, no device work).  Deals n_queries queries (lengths q_lengths, host)
+ * longest first, each to the stream with the fewest strips so far, to
+ * 2 x n_pairs streams of `rows`-row strips (each query padded to whole
+ * strips, at least one); streams 2k and 2k + 1 form pair k, and the queries
+ * of each pair are then split between its two streams so that the longer
+ * one is as short as possible.  This is the layout sw_plan_search uses once
+ * it has chosen the number of pairs (the batching of Section III-A with two
+ * queries per 32-bit word).
+ *   strips:   4 int32 per strip, for at most strip_capacity strips: the query
+ *             of half 0, its first row | 0x80000000 when the strip is that
+ *             query's last; the same for half 1 (query -1: an empty half);
+ *   pairs:    2 int32 per stream pair (n_pairs pairs): first strip, strips;
+ *   n_strips: the table's length.
+ * Errors: SW_EINVAL (rows not 16, 24 or 32; n_pairs outside 1..n_queries/2;
+ * a negative length; a NULL buffer), SW_EBUSY (more than strip_capacity
+ * strips). */
+sw_status sw_query_streams(const int32_t* q_lengths, int32_t n_queries, int32_t rows,
+                           int32_t n_pairs, int32_t* strips, int64_t strip_capacity,
+                           int32_t* pairs, int64_t* n_strips);
+
 /* Integer-pipe microbenchmark (Section III-B, Eq. 4: the throughput term,
  * measured instead of looked up).  op selects an instruction kind (0 iadd,
  * 1 imax, 2 viaddmax_s32, 3 viaddmax_s16x2, 4 viaddmax_s16x2_relu,

@@ -974,6 +974,32 @@ static int32_t plan_streams_long(sw_plan* p, const HostBatch& hb, int32_t nq, in
   return 0.85 * two < one ? K : 0;
 }
 
+// The stream layout alone, for a given number of stream pairs (host only).
+extern "C" sw_status sw_query_streams(const int32_t* q_lengths, int32_t n_queries, int32_t rows,
+                                      int32_t n_pairs, int32_t* strips, int64_t strip_capacity,
+                                      int32_t* pairs, int64_t* n_strips) {
+  sw_clear_error();
+  if (rows != 16 && rows != 24 && rows != 32)
+    return sw_set_error(SW_EINVAL, "rows must be 16, 24 or 32");
+  if (n_queries < 2 || n_pairs < 1 || n_pairs > n_queries / 2)
+    return sw_set_error(SW_EINVAL, "n_pairs must be 1..n_queries/2 (n_queries %d)", n_queries);
+  if (!q_lengths || !strips || !pairs || !n_strips || strip_capacity < 0)
+    return sw_set_error(SW_EINVAL, "sw_query_streams: NULL buffer or negative capacity");
+  HostBatch hb;
+  hb.len.assign(q_lengths, q_lengths + n_queries);
+  for (int32_t i = 0; i < n_queries; i++)
+    if (hb.len[i] < 0) return sw_set_error(SW_EINVAL, "q_lengths[%d] < 0", i);
+  hb.order.resize(n_queries);
+  std::iota(hb.order.begin(), hb.order.end(), 0);
+  std::stable_sort(hb.order.begin(), hb.order.end(),
+                   [&](int32_t a, int32_t b) { return hb.len[a] > hb.len[b]; });
+  const int32_t K = deal_streams(hb, n_queries, rows, n_pairs, 1.0, 1.0, 0.0, 0.0,
+                                 (int4*)strips, (int2*)pairs, 0, strip_capacity, n_strips);
+  if (K == 0) return sw_set_error(SW_EBUSY, "the strip table exceeds %lld strips",
+                                  (long long)strip_capacity);
+  return SW_OK;
+}
+
 // Stages a batch into the plan and enqueues everything up to (not including)
 // the copy of the scores to a host buffer.
 static sw_status plan_enqueue(sw_plan* p, const HostBatch& hb, int32_t nq, int32_t gap_open,

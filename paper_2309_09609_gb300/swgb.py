@@ -99,6 +99,7 @@ def lib():
             "sw_intpeak": (i32, [i32, i32, i32, i32, P]),
             "sw_search_pairs_noalloc": (i32, [P, P, P, i32, P, P, P, i32, i32, i32, P, P, P]),
             "sw_align": (i32, [P, P, P, i32, P, P, i32, i32, i32, P, P, P, i64, P]),
+            "sw_query_streams": (i32, [P, i32, i32, i32, P, i64, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -451,3 +452,18 @@ def intpeak(op, blocks_per_sm: int = 8, threads: int = 256, iters: int = 20000):
     out = np.zeros(3, dtype=np.float64)
     _check(lib().sw_intpeak(code, blocks_per_sm, threads, iters, _ptr(out)))
     return float(out[0]), float(out[1]), float(out[2])
+
+
+def query_streams(q_lengths, rows: int = 32, n_pairs: int = 1):
+    """The query streams of the two-query kernels (sw_query_streams, host
+    only): (strips, pairs) -- strips an (n, 4) int32 array (query of half 0,
+    first row | 0x80000000 on its last strip, the same for half 1; query -1
+    for an empty half), pairs a (n_pairs, 2) array (first strip, strips)."""
+    lens = np.ascontiguousarray(np.asarray(q_lengths, dtype=np.int32))
+    cap = 2 * (int(lens.clip(min=0).sum()) // 16 + 2 * len(lens)) + 16
+    strips = np.zeros((cap, 4), dtype=np.int32)
+    pairs = np.zeros((max(int(n_pairs), 1), 2), dtype=np.int32)
+    n = ctypes.c_int64(0)
+    _check(lib().sw_query_streams(_ptr(lens), len(lens), int(rows), int(n_pairs), _ptr(strips),
+                                  cap, _ptr(pairs), ctypes.byref(n)))
+    return strips[:n.value].copy(), pairs[:int(n_pairs)].copy()
