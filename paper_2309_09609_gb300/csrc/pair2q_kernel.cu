@@ -150,6 +150,11 @@ pair2q_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Sc
   gap_words<G>(P, GO2, NGE2, MGO);
   const uint32_t one = (uint32_t)P->one;
   const uint32_t lane_off = (uint32_t)(lane * P2_LANE_BYTES);
+  // lane 0 takes its top border from the scratch row, the others from the
+  // lane above: x * is0 + y * not0 picks one word exactly (a product by 0 or
+  // 1), as two multiply-adds on the FMA pipe instead of a select on the
+  // busier ALU pipe
+  const uint32_t is0 = lane == 0 ? 1u : 0u, not0 = 1u - is0;
   for (;;) {
     if (threadIdx.x == 0) *s_item = atomicAdd(&st->pair2_work, 1ull);
     __syncthreads();
@@ -250,10 +255,8 @@ pair2q_kernel(DbView db, const SearchParams* __restrict__ P, SearchState* st, Sc
             bv = bq[U];
             bq[U] = hb[t + 4];
           }
-          if (lane == 0) {
-            in_h = bv.x;
-            in_f = bv.y;
-          }
+          in_h = imad(bv.x, is0, imad(in_h, not0, 0u));
+          in_f = imad(bv.y, is0, imad(in_f, not0, 0u));
           if constexpr (decltype(masked)::value) {
             in_h = (in_h & keep) | gtop;  // H(0, j) = 0 above a query's first row
             in_f &= keep;                 // F(1, j) = -Go
