@@ -85,3 +85,21 @@ def test_l2_flush_only_when_the_database_fits_in_l2():
     assert bench.l2_flush_bytes(36_036_930) == 2 * bench.L2_BYTES  # batched-uneven database
     assert bench.l2_note(205_000_000).startswith("no flush")
     assert bench.l2_note(36_036_930).startswith("L2 flushed")
+
+
+def test_roofline_names_the_dominant_kernel_and_counts_its_layouts_ops():
+    # two-query layouts count 2.25 ALU lane-ops per cell, two-subject ones 2.75
+    stats = {"inter2_items": 4, "pair2_items": 0, "cells": 10 ** 12, "inter_cells": 9 * 10 ** 11}
+    t = {"stats": stats, "kernel_ms": [100.0, 100.0], "pair_ms": [20.0], "recompute_ms": [0.01]}
+    r = bench.roofline(t, 20.0, "test", 2070.0, lambda k: 123 if k == "inter2q_kernel" else None)
+    assert r["kernel"].startswith("inter2q_kernel") and r["traffic"] == 123
+    assert r["alu_ops_per_cell"] == bench.TWO_QUERY_ALU_OPS_PER_CELL == 2.25
+    assert abs(r["achieved"] - 2.25 * 9e11 / 0.1 / 1e12) < 1e-3 and abs(r["frac"] - r["achieved"] / 20.0) < 1e-4
+    pair = r["kernels"]["pair_kernel (packed intra-task)"]
+    assert pair["alu_ops_per_cell"] == bench.PACKED_ALU_OPS_PER_CELL == 2.75
+    # the long workload: the pair kernel dominates, two queries per word
+    stats = {"inter2_items": 0, "pair2_items": 8, "cells": 10 ** 12, "inter_cells": 0}
+    t = {"stats": stats, "kernel_ms": [0.01], "pair_ms": [500.0], "recompute_ms": [5.0]}
+    r = bench.roofline(t, 20.0, "test", 2070.0, lambda k: 7 if k == "pair2q_kernel" else None)
+    assert r["kernel"].startswith("pair2q_kernel") and r["traffic"] == 7
+    assert r["alu_ops_per_cell"] == 2.25 and r["pair_kernel_ms"] == 500.0
