@@ -993,10 +993,18 @@ extern "C" sw_status sw_query_streams(const int32_t* q_lengths, int32_t n_querie
   std::iota(hb.order.begin(), hb.order.end(), 0);
   std::stable_sort(hb.order.begin(), hb.order.end(),
                    [&](int32_t a, int32_t b) { return hb.len[a] > hb.len[b]; });
-  const int32_t K = deal_streams(hb, n_queries, rows, n_pairs, 1.0, 1.0, 0.0, 0.0,
-                                 (int4*)strips, (int2*)pairs, 0, strip_capacity, n_strips);
+  // built in aligned storage, then copied: the caller's buffers need only
+  // int32 alignment
+  int64_t bound = 0;  // the table is at most every query's strips long
+  for (int32_t i = 0; i < n_queries; i++) bound += std::max<int64_t>(1, (hb.len[i] + rows - 1) / rows);
+  std::vector<int4> tab((size_t)std::min(strip_capacity, bound));
+  std::vector<int2> pr((size_t)n_pairs);
+  const int32_t K = deal_streams(hb, n_queries, rows, n_pairs, 1.0, 1.0, 0.0, 0.0, tab.data(),
+                                 pr.data(), 0, strip_capacity, n_strips);
   if (K == 0) return sw_set_error(SW_EBUSY, "the strip table exceeds %lld strips",
                                   (long long)strip_capacity);
+  memcpy(strips, tab.data(), sizeof(int4) * (size_t)*n_strips);
+  memcpy(pairs, pr.data(), sizeof(int2) * (size_t)K);
   return SW_OK;
 }
 
